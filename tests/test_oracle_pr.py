@@ -1,0 +1,124 @@
+"""Pins for the phase-retrieval oracle: the propagator of Eq. (23) and its
+adjoint, the gradient of Eq. (27) against FP64 finite differences of Eq. (24),
+the error-reduction identity for a unitary A, and Algorithm 1 / Eq. (14)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pr
+from oracle.fgp import primal_value
+from oracle.ops import DT, Constraint, tv
+from phantoms import angular_spectrum_tf, fresnel_tf, pr_object, simulate_intensity
+
+CT = torch.complex128
+
+
+def rand_c(m, n, seed, scale=1.0):
+    g = torch.Generator().manual_seed(seed)
+    return torch.complex(scale * torch.randn(m, n, generator=g, dtype=DT),
+                         scale * torch.randn(m, n, generator=g, dtype=DT))
+
+
+def test_propagator_adjoint():
+    m, n, M, N = 12, 10, 24, 20
+    H = torch.tensor(fresnel_tf(M, N, 532e-9, 2e-6, 5e-3))
+    x, z = rand_c(m, n, 1), rand_c(m, n, 2)
+    lhs = torch.vdot(pr.propagate(x, H).flatten(), z.flatten())
+    rhs = torch.vdot(x.flatten(), pr.propagate_adjoint(z, H).flatten())
+    assert abs(complex(lhs - rhs)) < 1e-12 * abs(complex(lhs))
+
+
+def test_propagator_unpadded_is_unitary_and_matches_eq23():
+    m = n = 16
+    H = torch.tensor(angular_spectrum_tf(m, n, 500e-9, 5e-6, 5e-3))
+    assert float((H.abs() - 1).abs().max()) < 1e-12       # no evanescent waves at these settings
+    x = rand_c(m, n, 3)
+    Ax = pr.propagate(x, H)
+    assert abs(float(Ax.abs().pow(2).sum()) - float(x.abs().pow(2).sum())) < 1e-10 * float(x.abs().pow(2).sum())
+    # Eq. (23) by an explicit DFT matrix (no FFT): F^{-1} diag(H) F
+    W = torch.tensor(np.exp(-2j * np.pi * np.outer(np.arange(m), np.arange(m)) / m))
+    Fx = W @ x @ W.T
+    back = (W.conj() @ (Fx * H) @ W.conj().T) / (m * n)
+    assert float((back - Ax).abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("padded", [False, True])
+def test_fidelity_gradient_finite_differences(padded):
+    m, n = 8, 8
+    M, N = (16, 16) if padded else (8, 8)
+    H = torch.tensor(fresnel_tf(M, N, 532e-9, 2e-6, 5e-3))
+    x_gt = torch.tensor(pr_object(m, n, seed=5, blur_sigma=1.0))
+    sqrt_y = torch.tensor(np.sqrt(simulate_intensity(x_gt.numpy(), H.numpy(), seed=1, photons=0)))
+    x = x_gt + 0.1 * rand_c(m, n, 7)
+    g = pr.fidelity_grad(x, sqrt_y, H)
+    h = 1e-6
+    for j in range(m):
+        for k in range(0, n, 3):
+            for unit in (1.0, 1j):
+                e = torch.zeros(m, n, dtype=CT)
+                e[j, k] = unit
+                fd = (pr.fidelity(x + h * e, sqrt_y, H) - pr.fidelity(x - h * e, sqrt_y, H)) / (2 * h)
+                an = float(g[j, k].real) if unit == 1.0 else float(g[j, k].imag)
+                assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
+def test_error_reduction_identity():
+    # A unitary (no padding, |H| = 1): x - grad F(x) = A^*(sqrt(y) * A x / |A x|)
+    m = n = 10
+    H = torch.tensor(fresnel_tf(m, n, 532e-9, 2e-6, 5e-3))
+    x = rand_c(m, n, 11)
+    sqrt_y = torch.rand(m, n, dtype=DT, generator=torch.Generator().manual_seed(3))
+    lhs = x - pr.fidelity_grad(x, sqrt_y, H)
+    xi = pr.propagate(x, H)
+    rhs = pr.propagate_adjoint(sqrt_y * xi / xi.abs(), H)
+    assert float((lhs - rhs).abs().max()) < 1e-12
+
+
+def test_zero_field_convention():
+    # A x = 0 everywhere: the unit phase is 1, so grad F = A^*(-sqrt(y))
+    m = n = 6
+    H = torch.tensor(fresnel_tf(m, n, 532e-9, 2e-6, 5e-3))
+    sqrt_y = torch.ones(m, n, dtype=DT)
+    g = pr.fidelity_grad(torch.zeros(m, n, dtype=CT), sqrt_y, H)
+    want = pr.propagate_adjoint(-sqrt_y.to(CT), H)
+    assert float((g - want).abs().max()) < 1e-14
+
+
+def _pr_problem(m=32, seed=3):
+    M = 2 * m
+    H = torch.tensor(fresnel_tf(M, M, 532e-9, 2e-6, 5e-3))
+    x_gt = pr_object(m, m, seed=seed, blur_sigma=2.0)
+    y = simulate_intensity(x_gt, H.numpy(), seed=seed + 1, photons=1e4)
+    sqrt_y = torch.tensor(np.sqrt(y))
+    x0 = pr.propagate_adjoint(sqrt_y.to(CT), H)
+    return H, sqrt_y, x0, x_gt
+
+
+def test_fista_decreases_objective_and_beats_ista():
+    H, sqrt_y, x0, _ = _pr_problem()
+    tau, gamma = 0.01, 1.0
+    C = Constraint(amp_max=1.0)
+
+    def objective(x):
+        return pr.fidelity(x, sqrt_y, H) + tau * float(tv(x.real, x.imag, "tv1_aniso"))
+
+    xf, _ = pr.fista_pr(x0, sqrt_y, H, tau, gamma, 40, 10, "tv1_aniso", 0.5, C)
+    xi, _ = pr.fista_pr(x0, sqrt_y, H, tau, gamma, 40, 10, "tv1_aniso", 0.5, C, accelerate=False)
+    f0 = objective(torch.complex(*[t for t in (x0.real / torch.clamp(x0.abs(), min=1), x0.imag / torch.clamp(x0.abs(), min=1))]))
+    assert objective(xf) < f0 and objective(xi) < f0
+    assert objective(xf) <= objective(xi)
+    assert float(xf.abs().max()) <= 1 + 1e-12          # x_K lies in C
+
+
+def test_fista_one_step_is_prox_of_gradient_step():
+    # K = 1: x_1 = prox_{gamma R}(x_0 - gamma grad F(x_0)), the prox being Algorithm 2
+    from oracle.fgp import fgp
+    H, sqrt_y, x0, _ = _pr_problem(16, 5)
+    tau, gamma = 0.02, 0.8
+    C = Constraint(amp_max=1.0)
+    x1, _ = pr.fista_pr(x0, sqrt_y, H, tau, gamma, 1, 7, "tv2_iso", 0.5, C)
+    v = x0 - gamma * pr.fidelity_grad(x0, sqrt_y, H)
+    res = fgp((v.real.clone(), v.imag.clone()), tau * gamma, 7, "tv2_iso", 0.5, C)
+    assert float((x1 - torch.complex(*res.x)).abs().max()) == 0.0
