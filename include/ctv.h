@@ -1,0 +1,159 @@
+/*
+ * ctv.h - C ABI of the GB300 complex constrained TV library.
+ *
+ * The library solves problem (1) of Gao & Cao, "A Complex Constrained Total
+ * Variation Image Denoising Algorithm with Application to Phase Retrieval"
+ * (arXiv 2109.05496):
+ *
+ *     min_{x in C}  1/2 ||x - b||_F^2 + lambda ||x||_TV                    (1)
+ *
+ * for complex images x, b, with the four complex TV seminorms of Eq. (7)-(10),
+ * by the dual fast gradient projection of Algorithm 2 (Prop. 1, Eq. (16)-(20)),
+ * and uses it as the proximal step of FISTA (Algorithm 1) for the TV-regularised
+ * phase-retrieval problem (24).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller, unless a
+ *   comment says "host". The library never frees them.
+ * - Complex images are complex64, interleaved (re, im), row-major, m rows
+ *   (index j) by n columns (index k), with a leading dimension ld >= n counted in
+ *   complex elements. Pointers must be 8-byte aligned.
+ * - The dual variable q = (r1, r2, s1, s2) of Prop. 1 is stored per pixel as a
+ *   float4 (r1, s1, r2, s2) = (Re p1, Im p1, Re p2, Im p2) on a dense m x n grid
+ *   (row stride n). p1 (vertical difference, Eq. (5)) is zero on row m-1 and p2
+ *   (horizontal difference) is zero on column n-1: those slots do not exist in
+ *   the paper and are kept at zero. Pointers must be 16-byte aligned.
+ * - Every call is asynchronous and stream-ordered on `stream` unless it takes a
+ *   host `stats` pointer, in which case it synchronises the stream before it
+ *   returns so that the statistics can be filled in.
+ * - Argument errors return CTV_EINVAL before anything is launched. A CUDA error
+ *   raised while launching returns CTV_ECUDA. No entry point ever aborts the
+ *   process.
+ * - Workspaces are caller-owned device buffers of the size the matching
+ *   *_workspace_size call returns, 256-byte aligned. The library allocates
+ *   device memory only inside the *_create calls of plans.
+ */
+#ifndef CTV_H
+#define CTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* ctv_stream;
+
+typedef enum {
+  CTV_OK = 0,
+  CTV_EINVAL = 1,      /* invalid argument; nothing was launched */
+  CTV_ENOMEM = 2,      /* a plan could not allocate its device memory */
+  CTV_ECUDA = 3,       /* a CUDA runtime or cuFFT call failed */
+  CTV_ETIMEOUT = 4,    /* reserved: a bounded device wait ran out */
+  CTV_ENONFINITE = 5,  /* reserved: non-finite input detected */
+  CTV_EUNSUPPORTED = 6 /* valid request that this build does not implement */
+} ctv_status;
+
+/* The four complex TV seminorms: Eq. (7) type-I isotropic, Eq. (8) type-I
+ * anisotropic, Eq. (9) type-II isotropic, Eq. (10) type-II anisotropic. */
+typedef enum {
+  CTV_TV1_ISO = 0,
+  CTV_TV1_ANISO = 1,
+  CTV_TV2_ISO = 2,
+  CTV_TV2_ANISO = 3
+} ctv_tv_type;
+
+/* The closed convex set C of problem (1), a product of per-pixel sets.
+ * amp_bound != 0 adds |x| <= amp_max (Eq. (25) with amp_max = 1; projection
+ * Eq. (26)). support_kind: 0 none; 1 rectangle rows [rect[0], rect[2]) x
+ * columns [rect[1], rect[3]) (x = 0 outside); 2 mask: device uint8 array of
+ * m x n bytes, row stride mask_ld, x = 0 where the byte is 0. */
+typedef struct {
+  int amp_bound;
+  float amp_max;
+  int support_kind;
+  int rect[4];
+  const uint8_t* mask;
+  int mask_ld;
+} ctv_constraint;
+
+/* Solver options.
+ * max_iters   K, the number of iterations of Algorithm 2 (>= 0).
+ * check_every evaluate primal, dual and gap every this many iterations (0: only
+ *             at the end).
+ * gap_tol     > 0 stops at the first check with gap <= gap_tol * max(primal, 1e-30);
+ *             later passes become no-ops on the device (no host synchronisation).
+ * alpha       the weight of Eq. (9)/(10), in [0, 1]; ignored by type I.
+ * warm_start  nonzero: q_0 = r_1 = the q held in dual_state on entry (t_1 = 1).
+ * config      kernel configuration index (see ctv_config_info); -1 picks one.  */
+typedef struct {
+  int max_iters;
+  int check_every;
+  double gap_tol;
+  float alpha;
+  int warm_start;
+  int config;
+} ctv_opts;
+
+/* Result statistics of one image. iters: iterations actually run; stopped:
+ * 1 if the gap test stopped the run; primal, dual, gap: P(x_K), the dual value
+ * of App. A (Eq. (30) times lambda) at q_K, and their difference. */
+typedef struct {
+  int iters;
+  int stopped;
+  double primal;
+  double dual;
+  double gap;
+  int status;
+} ctv_stats;
+
+const char* ctv_status_string(int status);
+int ctv_abi_version(void);
+
+/* Kernel configurations of the fused FGP pass: iterations per pass (temporal
+ * blocking depth) and the shared-memory region of one thread block. */
+int ctv_num_configs(void);
+int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads);
+
+/* --------------------------------------------------------------------------
+ * Denoising, problem (1), by Algorithm 2.
+ * b: input image(s); x: output x_K = P_C(b - lambda L^T(q_K)) (Eq. (18)).
+ * dual_state: NULL, or q (float4 per pixel, m x n per image) - read on entry
+ * when opts->warm_start is set, always overwritten with q_K on exit.
+ * lambda = 0 gives x = P_C(b). m = 1 and/or n = 1 are valid.
+ * -------------------------------------------------------------------------- */
+size_t ctv_denoise_workspace_size(int batch, int m, int n);
+
+int ctv_denoise(const void* b, void* x, int m, int n, int ld, float lambda,
+                const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                void* dual_state, void* workspace, size_t workspace_bytes,
+                ctv_stats* stats /* host, nullable */, ctv_stream stream);
+
+/* A batch of equally sized images, image i at b + i * batch_stride (complex
+ * elements, same for x), with per-image lambda in the DEVICE array lambdas
+ * (batch floats, each >= 0). stats: host array of batch entries, or NULL. */
+int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
+                        long long batch_stride, const float* lambdas,
+                        const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                        void* dual_state, void* workspace, size_t workspace_bytes,
+                        ctv_stats* stats, ctv_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Measurement (no counterpart in the paper). ctv_profile_enable(1) resets the
+ * counters and brackets every following launch of the fused FGP pass kernel
+ * with CUDA events on its stream; ctv_profile_read synchronises on those events
+ * and returns the summed kernel time in ms, the number of timed launches, the
+ * pixel-iterations they processed, and the number of kernel launches of the
+ * library since the last enable (counted whether or not timing is on).
+ * -------------------------------------------------------------------------- */
+int ctv_profile_enable(int on);
+int ctv_profile_read(double* pass_ms, long long* pass_launches, double* pass_pixel_iters,
+                     long long* all_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTV_H */

@@ -1,0 +1,181 @@
+"""Python entry points over the C ABI (argument marshalling only).
+
+``ctv_denoise`` / ``ctv_denoise_batched`` mirror the C calls of the same names
+on torch tensors; ``denoise`` is the convenience form. torch supplies device
+memory and the current stream; all arithmetic runs in ``libctv.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple, Union
+
+import torch
+
+from . import _lib as L
+
+TV_TYPES = {"tv1_iso": 0, "tv1_aniso": 1, "tv2_iso": 2, "tv2_aniso": 3}
+
+
+def tv_code(tv: Union[str, int]) -> int:
+    if isinstance(tv, str):
+        if tv not in TV_TYPES:
+            raise ValueError("unknown TV type %r (one of %s)" % (tv, ", ".join(TV_TYPES)))
+        return TV_TYPES[tv]
+    return int(tv)
+
+
+@dataclass
+class Constraint:
+    """The set C of problem (1): |x| <= amp_max (None: no bound; Eq. (25) uses 1),
+    an optional support rectangle (j0, k0, j1, k1) (half-open) or a support mask
+    (CUDA uint8/bool tensor, nonzero = inside)."""
+    amp_max: Optional[float] = 1.0
+    rect: Optional[Tuple[int, int, int, int]] = None
+    mask: Optional[torch.Tensor] = None
+
+    def to_c(self) -> Tuple[L.CtvConstraint, object]:
+        c = L.CtvConstraint()
+        if self.amp_max is not None:
+            c.amp_bound, c.amp_max = 1, float(self.amp_max)
+        keep = None
+        if self.rect is not None:
+            c.support_kind = 1
+            for i, v in enumerate(self.rect):
+                c.rect[i] = int(v)
+        elif self.mask is not None:
+            mk = self.mask
+            if mk.dtype == torch.bool:
+                mk = mk.to(torch.uint8)
+            if not mk.is_cuda or mk.dim() != 2 or mk.stride(1) != 1:
+                raise ValueError("mask must be a 2-D CUDA tensor with unit column stride")
+            c.support_kind, c.mask, c.mask_ld = 2, mk.data_ptr(), mk.stride(0)
+            keep = mk
+        return c, keep
+
+
+NO_CONSTRAINT = Constraint(amp_max=None)
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def make_opts(iters: int, check_every: int = 0, gap_tol: float = 0.0, alpha: float = 0.5,
+              warm_start: bool = False, config: int = -1) -> L.CtvOpts:
+    o = L.CtvOpts()
+    o.max_iters, o.check_every, o.gap_tol = int(iters), int(check_every), float(gap_tol)
+    o.alpha, o.warm_start, o.config = float(alpha), int(bool(warm_start)), int(config)
+    return o
+
+
+def _check_image(t: torch.Tensor, name: str, ndim: int):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.complex64:
+        raise ValueError("%s must be complex64" % name)
+    if t.dim() != ndim or t.stride(-1) != 1:
+        raise ValueError("%s must be %d-D with unit column stride" % (name, ndim))
+
+
+def workspace(batch: int, m: int, n: int, device) -> torch.Tensor:
+    lib = L.load()
+    nbytes = lib.ctv_denoise_workspace_size(batch, m, n)
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def ctv_denoise(b: torch.Tensor, x: torch.Tensor, lam: float, C: Optional[Constraint], tv_type,
+                opts: L.CtvOpts, dual_state: Optional[torch.Tensor] = None,
+                ws: Optional[torch.Tensor] = None, want_stats: bool = False, stream=None):
+    """One image: the C call ``ctv_denoise`` on tensors. Returns a stats dict
+    when want_stats (this synchronises the stream), else None."""
+    lib = L.load()
+    _check_image(b, "b", 2)
+    _check_image(x, "x", 2)
+    m, n = b.shape
+    if x.shape != b.shape or x.stride(0) != b.stride(0):
+        raise ValueError("x must have b's shape and row stride")
+    if dual_state is not None and (dual_state.dtype != torch.float32 or not dual_state.is_contiguous()
+                                   or dual_state.numel() != 4 * m * n):
+        raise ValueError("dual_state must be a contiguous float32 tensor of 4*m*n values")
+    if ws is None:
+        ws = workspace(1, m, n, b.device)
+    cc, keep = (C or NO_CONSTRAINT).to_c()
+    st = L.CtvStats()
+    status = lib.ctv_denoise(b.data_ptr(), x.data_ptr(), m, n, b.stride(0), float(lam), C_ref(cc),
+                             tv_code(tv_type), C_ref(opts),
+                             dual_state.data_ptr() if dual_state is not None else None,
+                             ws.data_ptr(), ws.numel(), C_ref(st) if want_stats else None,
+                             _stream_ptr(stream))
+    L.check("ctv_denoise", status)
+    del keep
+    return st.as_dict() if want_stats else None
+
+
+def ctv_denoise_batched(b: torch.Tensor, x: torch.Tensor, lams: torch.Tensor, C: Optional[Constraint],
+                        tv_type, opts: L.CtvOpts, dual_state: Optional[torch.Tensor] = None,
+                        ws: Optional[torch.Tensor] = None, want_stats: bool = False, stream=None):
+    """Equally sized batch (B, m, n) with per-image lambda (CUDA float32 tensor
+    of B values): the C call ``ctv_denoise_batched``."""
+    lib = L.load()
+    _check_image(b, "b", 3)
+    _check_image(x, "x", 3)
+    B, m, n = b.shape
+    if x.shape != b.shape or x.stride() != b.stride():
+        raise ValueError("x must have b's shape and strides")
+    if not (lams.is_cuda and lams.dtype == torch.float32 and lams.numel() == B and lams.is_contiguous()):
+        raise ValueError("lams must be a contiguous CUDA float32 tensor with one value per image")
+    if dual_state is not None and (dual_state.dtype != torch.float32 or not dual_state.is_contiguous()
+                                   or dual_state.numel() != 4 * B * m * n):
+        raise ValueError("dual_state must be a contiguous float32 tensor of 4*B*m*n values")
+    if ws is None:
+        ws = workspace(B, m, n, b.device)
+    cc, keep = (C or NO_CONSTRAINT).to_c()
+    st = (L.CtvStats * B)()
+    status = lib.ctv_denoise_batched(b.data_ptr(), x.data_ptr(), B, m, n, b.stride(1), b.stride(0),
+                                     lams.data_ptr(), C_ref(cc), tv_code(tv_type), C_ref(opts),
+                                     dual_state.data_ptr() if dual_state is not None else None,
+                                     ws.data_ptr(), ws.numel(), st if want_stats else None,
+                                     _stream_ptr(stream))
+    L.check("ctv_denoise_batched", status)
+    del keep
+    return [s.as_dict() for s in st] if want_stats else None
+
+
+def C_ref(obj):
+    return C.byref(obj)
+
+
+def denoise(b: torch.Tensor, lam, tv: Union[str, int] = "tv1_iso", iters: int = 100,
+            C: Optional[Constraint] = Constraint(), alpha: float = 0.5, check_every: int = 0,
+            gap_tol: float = 0.0, dual_state: Optional[torch.Tensor] = None, warm_start: bool = False,
+            config: int = -1, return_stats: bool = False, out: Optional[torch.Tensor] = None):
+    """Solve problem (1) for one complex64 image (m, n) or a batch (B, m, n).
+
+    lam: a float, or for a batch a float / CUDA float32 tensor of B values.
+    Returns x (and the statistics when return_stats)."""
+    opts = make_opts(iters, check_every, gap_tol, alpha, warm_start, config)
+    x = out if out is not None else torch.empty_like(b)
+    if b.dim() == 2:
+        st = ctv_denoise(b, x, float(lam), C, tv, opts, dual_state, want_stats=return_stats)
+    elif b.dim() == 3:
+        if isinstance(lam, torch.Tensor):
+            lams = lam.to(device=b.device, dtype=torch.float32).contiguous()
+        else:
+            lams = torch.full((b.shape[0],), float(lam), dtype=torch.float32, device=b.device)
+        st = ctv_denoise_batched(b, x, lams, C, tv, opts, dual_state, want_stats=return_stats)
+    else:
+        raise ValueError("b must be (m, n) or (B, m, n)")
+    return (x, st) if return_stats else x
+
+
+def configs():
+    lib = L.load()
+    out = []
+    for i in range(lib.ctv_num_configs()):
+        T, W, H, NT = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        L.check("ctv_config_info", lib.ctv_config_info(i, C.byref(T), C.byref(W), C.byref(H), C.byref(NT)))
+        out.append({"config": i, "iters_per_pass": T.value, "region_w": W.value, "region_h": H.value,
+                    "threads": NT.value})
+    return out

@@ -1,0 +1,247 @@
+// Device building blocks of the fused FGP kernels (Algorithm 2 of Gao & Cao).
+//
+// Notation follows the paper: L maps an image to its finite differences
+// (Eq. (5)/(6)), L^T is its adjoint, P_C projects onto the per-pixel set C
+// (Eq. (26) plus a support), P_S projects the dual onto S (Eq. (20), (33),
+// (35), (37)). A dual pixel is a float4 (r1, s1, r2, s2) = (Re p1, Im p1,
+// Re p2, Im p2); p1 is zero on the last row and p2 on the last column, so the
+// paper's edge cases of Eq. (7)-(10), (17), (20), (34) follow from the
+// interior formulas.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ctv {
+
+enum { TV1_ISO = 0, TV1_ANISO = 1, TV2_ISO = 2, TV2_ANISO = 3 };
+
+// The per-pixel closed convex set C (a product set, so P_C is pointwise).
+struct ConsDev {
+  int amp;          // nonzero: |x| <= amax (Eq. (25))
+  float amax;
+  int sup;          // 0 none, 1 rectangle, 2 mask
+  int j0, k0, j1, k1;
+  const uint8_t* mask;
+  int mask_ld;
+};
+
+// Per-image solver record, kept in the caller's workspace.
+struct DevStats {
+  double acc[4];            // running sums of the gap reduction (fidelity, TV, dual part)
+  unsigned int blocks_done; // blocks of the current reduction that have finished
+  int stop;                 // set once the gap test has passed
+  int stop_set;             // dual buffer set holding q at the stop
+  int stop_iter;            // iteration at which the run stopped
+  int iters;                // iterations represented by the last evaluation
+  int status;
+  double primal, dual, gap; // last evaluation
+};
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+
+// P_C: support first (x = 0 outside), then the amplitude bound of Eq. (26):
+// x * amax / max{amax, |x|}.
+__device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev& c) {
+  if (c.sup == 1) {
+    if (gj < c.j0 || gj >= c.j1 || gk < c.k0 || gk >= c.k1) return make_float2(0.f, 0.f);
+  } else if (c.sup == 2) {
+    if (c.mask[(long long)gj * c.mask_ld + gk] == 0) return make_float2(0.f, 0.f);
+  }
+  if (c.amp) {
+    const float a2 = w.x * w.x + w.y * w.y;
+    if (a2 > c.amax * c.amax) {
+      const float s = c.amax * rsqrtf(a2);
+      w.x *= s;
+      w.y *= s;
+    }
+  }
+  return w;
+}
+
+// P_S for the four TV types. g = (r1, s1, r2, s2).
+template <int TV>
+__device__ __forceinline__ float4 proj_S(float4 g, float alpha) {
+  if (TV == TV1_ISO) {            // Eq. (20): joint 4-vector into the unit ball
+    const float nn = g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w;
+    if (nn > 1.f) {
+      const float s = rsqrtf(nn);
+      g.x *= s; g.y *= s; g.z *= s; g.w *= s;
+    }
+  } else if (TV == TV1_ANISO) {   // Eq. (33): p1 and p2 into the unit disk separately
+    const float n1 = g.x * g.x + g.y * g.y;
+    if (n1 > 1.f) { const float s = rsqrtf(n1); g.x *= s; g.y *= s; }
+    const float n2 = g.z * g.z + g.w * g.w;
+    if (n2 > 1.f) { const float s = rsqrtf(n2); g.z *= s; g.w *= s; }
+  } else if (TV == TV2_ISO) {     // Eq. (35): (r1, r2) into radius alpha, (s1, s2) into 1 - alpha
+    const float a = alpha, c = 1.f - alpha;
+    const float nr = g.x * g.x + g.z * g.z;
+    if (nr > a * a) { const float s = a * rsqrtf(nr); g.x *= s; g.z *= s; }
+    const float ns = g.y * g.y + g.w * g.w;
+    if (ns > c * c) { const float s = c * rsqrtf(ns); g.y *= s; g.w *= s; }
+  } else {                        // Eq. (37): componentwise clamps
+    const float a = alpha, c = 1.f - alpha;
+    g.x = fminf(fmaxf(g.x, -a), a);
+    g.z = fminf(fmaxf(g.z, -a), a);
+    g.y = fminf(fmaxf(g.y, -c), c);
+    g.w = fminf(fmaxf(g.w, -c), c);
+  }
+  return g;
+}
+
+// One pixel's share of TV(x) given its two differences d1 = x[j,k] - x[j+1,k]
+// and d2 = x[j,k] - x[j,k+1] (zero where the paper has no such difference):
+// the summand of Eq. (7), (8), (9) or (10).
+template <int TV>
+__device__ __forceinline__ float tv_term(float d1r, float d1i, float d2r, float d2i, float alpha) {
+  if (TV == TV1_ISO) return sqrtf(d1r * d1r + d1i * d1i + d2r * d2r + d2i * d2i);
+  if (TV == TV1_ANISO) return sqrtf(d1r * d1r + d1i * d1i) + sqrtf(d2r * d2r + d2i * d2i);
+  if (TV == TV2_ISO) return alpha * sqrtf(d1r * d1r + d2r * d2r) + (1.f - alpha) * sqrtf(d1i * d1i + d2i * d2i);
+  return alpha * (fabsf(d1r) + fabsf(d2r)) + (1.f - alpha) * (fabsf(d1i) + fabsf(d2i));
+}
+
+// Everything one pass over one image needs.
+struct Img {
+  const float2* b;      // complex64, row stride ld
+  int ld;
+  const float4* q_in;   // q_{k-1}, dense m x n
+  const float4* r_in;   // r_k
+  float4* q_out;        // q_{k+T-1}
+  float4* r_out;        // r_{k+T}
+  int m, n;
+  float lam, alpha;
+  ConsDev C;
+};
+
+// T iterations of Algorithm 2 on one tile, temporally blocked in shared memory.
+//
+// The block loads the dual state and b for an RW x RH region whose interior
+// ((RW - 2T) x (RH - 2T) pixels starting at image pixel (j0, k0)) it owns, and
+// then runs nsteps <= T iterations of
+//     phase 1:  x = P_C(b - lam L^T r)                 (reads r at self, up, left)
+//     phase 2:  q = P_S(r + L x / (8 lam))             (reads x at self, down, right)
+//               r' = q + beta_k (q - q_prev)            (Alg. 2, steps 3-5)
+// Each iteration invalidates one more ring of the region, so after T steps
+// exactly the interior is correct, and only the interior is written back.
+// Pixels outside the image hold r = x = 0, which is the boundary condition of
+// Eq. (5)/(6). q and b live in registers (each thread owns PPT pixels), r and
+// x in shared memory for the neighbours.
+template <int TV, int T, int RW, int RH, int NT>
+__device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const float* beta,
+                                         int nsteps, bool first) {
+  constexpr int R = RW * RH;
+  constexpr int PPT = R / NT;
+  static_assert(R % NT == 0, "region must split evenly over the threads");
+  extern __shared__ float4 smem4[];
+  float4* rs = smem4;
+  float2* xs = reinterpret_cast<float2*>(smem4 + R);
+  const int tid = threadIdx.x;
+  const int gj0 = j0 - T, gk0 = k0 - T;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+
+  float4 qreg[PPT];
+  float2 breg[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float4 q = z4, r = z4;
+    float2 bb = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)I.m && (unsigned)gk < (unsigned)I.n) {
+      bb = __ldg(I.b + (long long)gj * I.ld + gk);
+      if (!first) {
+        const long long o = (long long)gj * I.n + gk;
+        q = __ldg(I.q_in + o);
+        r = __ldg(I.r_in + o);
+      }
+    }
+    qreg[s] = q;
+    breg[s] = bb;
+    rs[i] = r;
+  }
+  __syncthreads();
+
+  const float lam = I.lam;
+  const float c8 = 1.f / (8.f * lam);   // 1/(16 lam^2) times the 2 lam of Eq. (19)
+  for (int it = 0; it < nsteps; ++it) {
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int i = tid + s * NT;
+      const int lj = i / RW, lk = i % RW;
+      const int gj = gj0 + lj, gk = gk0 + lk;
+      float2 xv = make_float2(0.f, 0.f);
+      if ((unsigned)gj < (unsigned)I.m && (unsigned)gk < (unsigned)I.n) {
+        const float4 rc = rs[i];
+        const float4 ru = lj > 0 ? rs[i - RW] : z4;
+        const float4 rl = lk > 0 ? rs[i - 1] : z4;
+        // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]
+        const float dre = rc.x - ru.x + rc.z - rl.z;
+        const float dim = rc.y - ru.y + rc.w - rl.w;
+        xv = proj_C(make_float2(breg[s].x - lam * dre, breg[s].y - lam * dim), gj, gk, I.C);
+      }
+      xs[i] = xv;
+    }
+    __syncthreads();
+    const float bt = beta[it];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int i = tid + s * NT;
+      const int lj = i / RW, lk = i % RW;
+      const int gj = gj0 + lj, gk = gk0 + lk;
+      if ((unsigned)gj < (unsigned)I.m && (unsigned)gk < (unsigned)I.n) {
+        const float2 xc = xs[i];
+        float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+        if (gj < I.m - 1 && lj < RH - 1) { const float2 xd = xs[i + RW]; d1r = xc.x - xd.x; d1i = xc.y - xd.y; }
+        if (gk < I.n - 1 && lk < RW - 1) { const float2 xr = xs[i + 1]; d2r = xc.x - xr.x; d2i = xc.y - xr.y; }
+        const float4 rc = rs[i];
+        const float4 qn = proj_S<TV>(f4(rc.x + c8 * d1r, rc.y + c8 * d1i, rc.z + c8 * d2r, rc.w + c8 * d2i), I.alpha);
+        const float4 qo = qreg[s];
+        rs[i] = f4(qn.x + bt * (qn.x - qo.x), qn.y + bt * (qn.y - qo.y),
+                   qn.z + bt * (qn.z - qo.z), qn.w + bt * (qn.w - qo.w));
+        qreg[s] = qn;
+      }
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    if (lj >= T && lj < RH - T && lk >= T && lk < RW - T &&
+        (unsigned)gj < (unsigned)I.m && (unsigned)gk < (unsigned)I.n) {
+      const long long o = (long long)gj * I.n + gk;
+      I.q_out[o] = qreg[s];
+      I.r_out[o] = rs[i];
+    }
+  }
+}
+
+// Block-wide FP64 sum of NV values; the result is valid in thread 0.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* smem, NV * NT/32 */) {
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * (NT / 32) + warp] = v[a];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = lane < NT / 32 ? red[a * (NT / 32) + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      v[a] = t;
+    }
+  }
+}
+
+}  // namespace ctv

@@ -1,0 +1,46 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "ctv.h"
+
+namespace ctv {
+
+struct ConsDev;
+
+// One denoising request, single image (lam) or equally sized batch (lam_dev).
+struct DenoiseCall {
+  const void* b;
+  void* x;
+  int batch, m, n, ld;
+  long long batch_stride;
+  float lam;
+  const float* lam_dev;
+  const ctv_constraint* C;
+  int tv;
+  const ctv_opts* opts;
+  void* dual_state;
+  void* workspace;
+  size_t workspace_bytes;
+  ctv_stats* stats;
+  ctv_stream stream;
+};
+
+ctv_status run_denoise(const DenoiseCall& c);
+size_t denoise_workspace_bytes(int batch, int m, int n);
+bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out);
+void nesterov_betas(int K, std::vector<double>* beta);
+int default_config(int m, int n, int iters);
+int num_configs();
+bool config_info(int i, int* T, int* RW, int* RH, int* NT);
+
+// Measurement hooks (prof.cu): count every launch; time fused passes when enabled.
+void count_launch();
+int prof_begin(cudaStream_t s);
+void prof_end(int slot, cudaStream_t s, double units);
+
+}  // namespace ctv

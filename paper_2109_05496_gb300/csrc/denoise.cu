@@ -1,0 +1,559 @@
+// Complex constrained TV denoising, problem (1), by Algorithm 2 (FGP).
+//
+// Kernels
+//   fgp_pass_kernel   T fused FGP iterations per launch on shared-memory tiles
+//                     (see fgp_tile in ctv_device.cuh).
+//   fgp_gap_kernel    x = P_C(b - lam L^T q) (Eq. (18)) together with the primal
+//                     value of problem (1), the dual value of App. A (Eq. (30)
+//                     times lam) and their gap, reduced in FP64; its last block
+//                     applies the stopping test and, for the final call, writes
+//                     the statistics. Later passes read the stop flag and return.
+// Host entry points: ctv_denoise, ctv_denoise_batched (declared in ctv.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ctv.h"
+#include "ctv_device.cuh"
+#include "ctv_host.h"
+
+namespace ctv {
+
+struct PassParams {
+  const float2* b;
+  long long b_stride;
+  int ld;
+  const float4* q_in;
+  const float4* r_in;
+  float4* q_out;
+  float4* r_out;
+  long long d_stride;
+  int m, n;
+  float lam;
+  const float* lam_dev;
+  float alpha;
+  ConsDev C;
+  const DevStats* st;
+  float beta[8];
+  int nsteps;
+  int first;
+};
+
+template <int TV, int T, int RW, int RH, int NT>
+__global__ void __launch_bounds__(NT) fgp_pass_kernel(PassParams p) {
+  const int z = blockIdx.z;
+  if (p.st != nullptr && *(volatile const int*)&p.st[z].stop) return;
+  Img I;
+  I.b = p.b + z * p.b_stride;
+  I.ld = p.ld;
+  I.q_in = p.q_in + z * p.d_stride;
+  I.r_in = p.r_in + z * p.d_stride;
+  I.q_out = p.q_out + z * p.d_stride;
+  I.r_out = p.r_out + z * p.d_stride;
+  I.m = p.m;
+  I.n = p.n;
+  float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
+  I.lam = lam > 0.f ? lam : 0.f;
+  I.alpha = p.alpha;
+  I.C = p.C;
+  fgp_tile<TV, T, RW, RH, NT>(I, blockIdx.y * (RH - 2 * T), blockIdx.x * (RW - 2 * T), p.beta,
+                              p.nsteps, p.first != 0);
+}
+
+struct GapParams {
+  const float2* b;
+  long long b_stride;
+  int ld;
+  const float4* qA;
+  const float4* qB;
+  long long d_stride;
+  int default_set;   // 0: qA, 1: qB, 2: dual_in
+  const float4* dual_in;
+  int zero_q;        // q = 0 (no iteration has run)
+  float2* x;         // nullable
+  long long x_stride;
+  float4* q_export;  // nullable, stride d_stride
+  int m, n;
+  float lam;
+  const float* lam_dev;
+  float alpha;
+  ConsDev C;
+  DevStats* st;
+  int iter;
+  double gap_tol;
+  int final_call;
+};
+
+constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
+
+// Region of GAP_RW x GAP_RH pixels with a one-pixel halo; the interior of
+// (GAP_RW-2) x (GAP_RH-2) pixels is evaluated. x at a pixel needs q at the pixel,
+// above and to the left; the TV summand needs x below and to the right.
+template <int TV>
+__global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
+  constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
+  __shared__ float4 qs[R];
+  __shared__ float2 xs[R];
+  __shared__ double red[4 * (NT / 32)];
+  __shared__ int last;
+  const int z = blockIdx.z;
+  DevStats* st = p.st + z;
+  const int stopped = *(volatile int*)&st->stop;
+  if (!p.final_call && stopped) return;
+  const int set = stopped ? st->stop_set : p.default_set;
+  const float4* q = set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in);
+  q += z * p.d_stride;
+  const float2* b = p.b + z * p.b_stride;
+  float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
+  const bool bad_lam = !(lam >= 0.f);
+  if (bad_lam) lam = 0.f;
+  const int m = p.m, n = p.n;
+  const int gj0 = blockIdx.y * (RH - 2) - 1, gk0 = blockIdx.x * (RW - 2) - 1;
+  const int tid = threadIdx.x;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const bool zq = p.zero_q != 0 && !stopped;
+
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
+    float4 v = z4;
+    if (!zq && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) v = __ldg(q + (long long)gj * n + gk);
+    qs[i] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float2 xv = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float4 qc = qs[i];
+      const float4 qu = lj > 0 ? qs[i - RW] : z4;
+      const float4 ql = lk > 0 ? qs[i - 1] : z4;
+      const float2 bb = __ldg(b + (long long)gj * p.ld + gk);
+      xv = proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)),
+                  gj, gk, p.C);
+    }
+    xs[i] = xv;
+  }
+  __syncthreads();
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float4 qc = qs[i];
+      const float4 qu = qs[i - RW];
+      const float4 ql = qs[i - 1];
+      const float2 bb = __ldg(b + (long long)gj * p.ld + gk);
+      const float dlr = lam * (qc.x - qu.x + qc.z - ql.z);   // lam (L^T q)
+      const float dli = lam * (qc.y - qu.y + qc.w - ql.w);
+      const float wr = bb.x - dlr, wi = bb.y - dli;
+      const float2 xc = xs[i];
+      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+      if (gj < m - 1) { const float2 xd = xs[i + RW]; d1r = xc.x - xd.x; d1i = xc.y - xd.y; }
+      if (gk < n - 1) { const float2 xr = xs[i + 1]; d2r = xc.x - xr.x; d2i = xc.y - xr.y; }
+      const float er = xc.x - bb.x, ei = xc.y - bb.y;
+      acc[0] += (double)(er * er + ei * ei);
+      acc[1] += (double)tv_term<TV>(d1r, d1i, d2r, d2i, p.alpha);
+      // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
+      const float hr = wr - xc.x, hi = wi - xc.y;
+      acc[2] += (double)(2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (double)(hr * hr + hi * hi);
+      if (p.x != nullptr) p.x[z * p.x_stride + (long long)gj * p.ld + gk] = xc;
+      if (p.q_export != nullptr) p.q_export[z * p.d_stride + (long long)gj * n + gk] = qc;
+    }
+  }
+  block_sum<NT, 3>(acc, red);
+  if (tid == 0) {
+    atomicAdd(&st->acc[0], acc[0]);
+    atomicAdd(&st->acc[1], acc[1]);
+    atomicAdd(&st->acc[2], acc[2]);
+    __threadfence();
+    const unsigned nblk = gridDim.x * gridDim.y;
+    last = (atomicAdd(&st->blocks_done, 1u) == nblk - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (last && tid == 0) {
+    __threadfence();
+    volatile double* a = st->acc;
+    const double fid = a[0], tvs = a[1], dual2 = a[2];
+    const double P = 0.5 * fid + (double)lam * tvs;
+    const double D = 0.5 * dual2;
+    st->primal = P;
+    st->dual = D;
+    st->gap = P - D;
+    if (bad_lam) st->status = CTV_EINVAL;
+    if (!p.final_call) {
+      st->iters = p.iter;
+      if (p.gap_tol > 0.0 && P - D <= p.gap_tol * fmax(P, 1e-30)) {
+        st->stop = 1;
+        st->stop_set = set;
+        st->stop_iter = p.iter;
+      }
+    } else {
+      st->iters = stopped ? st->stop_iter : p.iter;
+    }
+    a[0] = 0.0;
+    a[1] = 0.0;
+    a[2] = 0.0;
+    __threadfence();
+    st->blocks_done = 0u;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Configurations of the fused pass
+// ----------------------------------------------------------------------------
+struct Cfg {
+  int T, RW, RH, NT;
+};
+static const Cfg kCfgs[] = {
+    {1, 64, 16, 256},
+    {2, 64, 32, 256},
+    {4, 64, 32, 256},
+    {4, 64, 64, 512},
+    {8, 64, 64, 512},
+};
+static const int kNumCfgs = (int)(sizeof(kCfgs) / sizeof(kCfgs[0]));
+
+template <int TV, int T, int RW, int RH, int NT>
+static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
+  constexpr size_t smem = (size_t)RW * RH * (sizeof(float4) + sizeof(float2));
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<TV, T, RW, RH, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  fgp_pass_kernel<TV, T, RW, RH, NT><<<grid, NT, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TV>
+static cudaError_t launch_pass_tv(int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return launch_pass_t<TV, 1, 64, 16, 256>(p, grid, s);
+    case 1: return launch_pass_t<TV, 2, 64, 32, 256>(p, grid, s);
+    case 2: return launch_pass_t<TV, 4, 64, 32, 256>(p, grid, s);
+    case 3: return launch_pass_t<TV, 4, 64, 64, 512>(p, grid, s);
+    case 4: return launch_pass_t<TV, 8, 64, 64, 512>(p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
+  switch (tv) {
+    case TV1_ISO: return launch_pass_tv<TV1_ISO>(cfg, p, grid, s);
+    case TV1_ANISO: return launch_pass_tv<TV1_ANISO>(cfg, p, grid, s);
+    case TV2_ISO: return launch_pass_tv<TV2_ISO>(cfg, p, grid, s);
+    case TV2_ANISO: return launch_pass_tv<TV2_ANISO>(cfg, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
+  dim3 grid((p.n + GAP_RW - 3) / (GAP_RW - 2), (p.m + GAP_RH - 3) / (GAP_RH - 2), batch);
+  switch (tv) {
+    case TV1_ISO: fgp_gap_kernel<TV1_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
+    case TV1_ANISO: fgp_gap_kernel<TV1_ANISO><<<grid, GAP_NT, 0, s>>>(p); break;
+    case TV2_ISO: fgp_gap_kernel<TV2_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
+    case TV2_ANISO: fgp_gap_kernel<TV2_ANISO><<<grid, GAP_NT, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int default_config(int m, int n, int iters) {
+  (void)m;
+  (void)n;
+  if (iters < 2) return 0;
+  return 2;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t denoise_workspace_bytes(int batch, int m, int n) {
+  if (batch <= 0 || m <= 0 || n <= 0) return 0;
+  const size_t px = (size_t)batch * m * n;
+  return align256((size_t)batch * sizeof(DevStats)) + 4 * align256(px * sizeof(float4));
+}
+
+bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out) {
+  memset(out, 0, sizeof(*out));
+  if (C == nullptr) return true;
+  if (C->amp_bound) {
+    if (!(C->amp_max >= 0.f) || isinf(C->amp_max)) return false;
+    out->amp = 1;
+    out->amax = C->amp_max;
+  }
+  if (C->support_kind == 1) {
+    out->sup = 1;
+    out->j0 = C->rect[0];
+    out->k0 = C->rect[1];
+    out->j1 = C->rect[2];
+    out->k1 = C->rect[3];
+  } else if (C->support_kind == 2) {
+    if (C->mask == nullptr || C->mask_ld < n) return false;
+    out->sup = 2;
+    out->mask = C->mask;
+    out->mask_ld = C->mask_ld;
+  } else if (C->support_kind != 0) {
+    return false;
+  }
+  (void)m;
+  return true;
+}
+
+void nesterov_betas(int K, std::vector<double>* beta) {
+  // t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, beta_k = (t_k - 1) / t_{k+1} (Alg. 2, steps 4-5)
+  beta->assign((size_t)K + 1, 0.0);
+  double t = 1.0;
+  for (int k = 1; k <= K; ++k) {
+    const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    (*beta)[k] = (t - 1.0) / tn;
+    t = tn;
+  }
+}
+
+ctv_status run_denoise(const DenoiseCall& c) {
+  if (c.b == nullptr || c.x == nullptr || c.workspace == nullptr) return CTV_EINVAL;
+  if (c.batch <= 0 || c.m <= 0 || c.n <= 0 || c.ld < c.n) return CTV_EINVAL;
+  if (c.batch > 65535) return CTV_EINVAL;
+  if (c.lam_dev == nullptr && (!(c.lam >= 0.f) || isinf(c.lam))) return CTV_EINVAL;
+  if (c.tv < 0 || c.tv > 3) return CTV_EINVAL;
+  if (((uintptr_t)c.b & 7) || ((uintptr_t)c.x & 7) || ((uintptr_t)c.workspace & 255)) return CTV_EINVAL;
+  if (c.dual_state != nullptr && ((uintptr_t)c.dual_state & 15)) return CTV_EINVAL;
+  const ctv_opts* o = c.opts;
+  const int K = o ? o->max_iters : 0;
+  const int check_every = o ? o->check_every : 0;
+  const double gap_tol = o ? o->gap_tol : 0.0;
+  const float alpha = o ? o->alpha : 0.5f;
+  const int warm = o ? o->warm_start : 0;
+  int cfg = o ? o->config : -1;
+  if (K < 0 || check_every < 0 || !(gap_tol >= 0.0) || !(alpha >= 0.f && alpha <= 1.f)) return CTV_EINVAL;
+  if (warm && c.dual_state == nullptr) return CTV_EINVAL;
+  if (cfg >= kNumCfgs || cfg < -1) return CTV_EINVAL;
+  if (cfg < 0) cfg = default_config(c.m, c.n, K);
+  ConsDev C;
+  if (!convert_constraint(c.C, c.m, c.n, &C)) return CTV_EINVAL;
+  if (c.workspace_bytes < denoise_workspace_bytes(c.batch, c.m, c.n)) return CTV_EINVAL;
+
+  cudaStream_t s = (cudaStream_t)c.stream;
+  const size_t px = (size_t)c.m * c.n;
+  char* ws = (char*)c.workspace;
+  DevStats* st = (DevStats*)ws;
+  size_t off = align256((size_t)c.batch * sizeof(DevStats));
+  float4* set_q[2];
+  float4* set_r[2];
+  const size_t dbytes = align256((size_t)c.batch * px * sizeof(float4));
+  set_q[0] = (float4*)(ws + off); off += dbytes;
+  set_r[0] = (float4*)(ws + off); off += dbytes;
+  set_q[1] = (float4*)(ws + off); off += dbytes;
+  set_r[1] = (float4*)(ws + off); off += dbytes;
+
+  if (cudaMemsetAsync(st, 0, (size_t)c.batch * sizeof(DevStats), s) != cudaSuccess) return CTV_ECUDA;
+
+  const bool lam_zero = c.lam_dev == nullptr && c.lam == 0.f;
+  const Cfg& cf = kCfgs[cfg];
+  GapParams g;
+  memset(&g, 0, sizeof(g));
+  g.b = (const float2*)c.b;
+  g.b_stride = c.batch_stride;
+  g.ld = c.ld;
+  g.qA = set_q[0];
+  g.qB = set_q[1];
+  g.d_stride = (long long)px;
+  g.dual_in = (const float4*)c.dual_state;
+  g.m = c.m;
+  g.n = c.n;
+  g.lam = c.lam;
+  g.lam_dev = c.lam_dev;
+  g.alpha = alpha;
+  g.C = C;
+  g.st = st;
+  g.gap_tol = gap_tol;
+
+  int last_set = -1;   // -1: no pass has run
+  if (K > 0 && !lam_zero) {
+    std::vector<double> beta;
+    nesterov_betas(K, &beta);
+    PassParams p;
+    memset(&p, 0, sizeof(p));
+    p.b = (const float2*)c.b;
+    p.b_stride = c.batch_stride;
+    p.ld = c.ld;
+    p.d_stride = (long long)px;
+    p.m = c.m;
+    p.n = c.n;
+    p.lam = c.lam;
+    p.lam_dev = c.lam_dev;
+    p.alpha = alpha;
+    p.C = C;
+    p.st = st;
+    dim3 grid((c.n + (cf.RW - 2 * cf.T) - 1) / (cf.RW - 2 * cf.T),
+              (c.m + (cf.RH - 2 * cf.T) - 1) / (cf.RH - 2 * cf.T), c.batch);
+    if (grid.y > 65535) return CTV_EINVAL;
+    int k = 1;
+    int out = 0;
+    const float4* q_in = (const float4*)c.dual_state;
+    const float4* r_in = (const float4*)c.dual_state;
+    bool first = !warm;
+    while (k <= K) {
+      int steps = K - k + 1;
+      if (steps > cf.T) steps = cf.T;
+      if (check_every > 0) {
+        const int to_check = check_every - ((k - 1) % check_every);
+        if (steps > to_check) steps = to_check;
+      }
+      for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
+      p.nsteps = steps;
+      p.first = first ? 1 : 0;
+      p.q_in = q_in;
+      p.r_in = r_in;
+      p.q_out = set_q[out];
+      p.r_out = set_r[out];
+      const int slot = prof_begin(s);
+      if (launch_pass(c.tv, cfg, p, grid, s) != cudaSuccess) return CTV_ECUDA;
+      count_launch();
+      prof_end(slot, s, (double)c.batch * (double)px * (double)steps);
+      first = false;
+      k += steps;
+      last_set = out;
+      q_in = set_q[out];
+      r_in = set_r[out];
+      out ^= 1;
+      if (check_every > 0 && (k - 1) % check_every == 0 && k - 1 < K) {
+        g.default_set = last_set;
+        g.zero_q = 0;
+        g.x = nullptr;
+        g.q_export = nullptr;
+        g.iter = k - 1;
+        g.final_call = 0;
+        if (launch_gap(c.tv, g, c.batch, s) != cudaSuccess) return CTV_ECUDA;
+        count_launch();
+      }
+    }
+  }
+  // finalize: x = P_C(b - lam L^T q_K), final statistics, optional export of q_K
+  g.x = (float2*)c.x;
+  g.x_stride = c.batch_stride;
+  g.q_export = (float4*)c.dual_state;
+  g.final_call = 1;
+  g.iter = (K > 0 && !lam_zero) ? K : 0;
+  if (last_set >= 0) {
+    g.default_set = last_set;
+    g.zero_q = 0;
+  } else if (warm) {
+    g.default_set = 2;   // the warm-start dual itself
+    g.zero_q = lam_zero ? 1 : 0;
+  } else {
+    g.default_set = 0;
+    g.zero_q = 1;
+  }
+  if (warm && last_set < 0 && g.q_export == g.dual_in) g.q_export = nullptr;  // unchanged
+  if (launch_gap(c.tv, g, c.batch, s) != cudaSuccess) return CTV_ECUDA;
+  count_launch();
+
+  if (c.stats != nullptr) {
+    std::vector<DevStats> hs((size_t)c.batch);
+    if (cudaMemcpyAsync(hs.data(), st, (size_t)c.batch * sizeof(DevStats), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return CTV_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CTV_ECUDA;
+    for (int i = 0; i < c.batch; ++i) {
+      c.stats[i].iters = hs[i].iters;
+      c.stats[i].stopped = hs[i].stop;
+      c.stats[i].primal = hs[i].primal;
+      c.stats[i].dual = hs[i].dual;
+      c.stats[i].gap = hs[i].gap;
+      c.stats[i].status = hs[i].status;
+    }
+  }
+  return CTV_OK;
+}
+
+int num_configs() { return kNumCfgs; }
+bool config_info(int i, int* T, int* RW, int* RH, int* NT) {
+  if (i < 0 || i >= kNumCfgs) return false;
+  if (T) *T = kCfgs[i].T;
+  if (RW) *RW = kCfgs[i].RW;
+  if (RH) *RH = kCfgs[i].RH;
+  if (NT) *NT = kCfgs[i].NT;
+  return true;
+}
+
+}  // namespace ctv
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+extern "C" {
+
+size_t ctv_denoise_workspace_size(int batch, int m, int n) { return ctv::denoise_workspace_bytes(batch, m, n); }
+
+int ctv_denoise(const void* b, void* x, int m, int n, int ld, float lambda, const ctv_constraint* C,
+                int tv_type, const ctv_opts* opts, void* dual_state, void* workspace, size_t workspace_bytes,
+                ctv_stats* stats, ctv_stream stream) {
+  ctv::DenoiseCall c;
+  memset(&c, 0, sizeof(c));
+  c.b = b;
+  c.x = x;
+  c.batch = 1;
+  c.m = m;
+  c.n = n;
+  c.ld = ld;
+  c.batch_stride = 0;
+  c.lam = lambda;
+  c.lam_dev = nullptr;
+  c.C = C;
+  c.tv = tv_type;
+  c.opts = opts;
+  c.dual_state = dual_state;
+  c.workspace = workspace;
+  c.workspace_bytes = workspace_bytes;
+  c.stats = stats;
+  c.stream = stream;
+  return ctv::run_denoise(c);
+}
+
+int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld, long long batch_stride,
+                        const float* lambdas, const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                        void* dual_state, void* workspace, size_t workspace_bytes, ctv_stats* stats,
+                        ctv_stream stream) {
+  if (lambdas == nullptr || ((uintptr_t)lambdas & 3)) return CTV_EINVAL;
+  if (batch > 1 && batch_stride < (long long)m * ld) return CTV_EINVAL;
+  ctv::DenoiseCall c;
+  memset(&c, 0, sizeof(c));
+  c.b = b;
+  c.x = x;
+  c.batch = batch;
+  c.m = m;
+  c.n = n;
+  c.ld = ld;
+  c.batch_stride = batch_stride;
+  c.lam = 0.f;
+  c.lam_dev = lambdas;
+  c.C = C;
+  c.tv = tv_type;
+  c.opts = opts;
+  c.dual_state = dual_state;
+  c.workspace = workspace;
+  c.workspace_bytes = workspace_bytes;
+  c.stats = stats;
+  c.stream = stream;
+  return ctv::run_denoise(c);
+}
+
+int ctv_num_configs(void) { return ctv::num_configs(); }
+
+int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads) {
+  return ctv::config_info(config, iters_per_pass, region_w, region_h, threads) ? CTV_OK : CTV_EINVAL;
+}
+
+}  // extern "C"
