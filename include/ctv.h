@@ -142,6 +142,82 @@ int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
                         ctv_stats* stats, ctv_stream stream);
 
 /* --------------------------------------------------------------------------
+ * Batched denoising of many images of uneven sizes (problem (1) per image).
+ * Each image has its own shape, lambda, alpha, TV type and C; all share
+ * opts->max_iters, check_every and gap_tol (warm_start must be 0; config -1
+ * picks one). ctv_plan_create copies the descriptors, allocates the plan's
+ * device memory (dual state 64 bytes per pixel plus work lists) and captures the
+ * whole schedule - one launch per pass over the tiles of all images - into a
+ * CUDA graph; ctv_plan_execute replays it on `stream` (asynchronous). The b and
+ * x pointers of the descriptors must stay valid while the plan is used.
+ * -------------------------------------------------------------------------- */
+typedef struct {
+  const void* b;      /* device complex64 input, row stride ld */
+  void* x;            /* device complex64 output, row stride ld */
+  int m, n, ld;
+  float lambda;       /* >= 0 */
+  float alpha;        /* type-II weight, [0, 1] */
+  int tv_type;        /* ctv_tv_type */
+  ctv_constraint C;
+} ctv_image_desc;
+
+typedef struct ctv_plan ctv_plan;
+
+int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts, ctv_plan** out);
+int ctv_plan_execute(ctv_plan* plan, ctv_stream stream);
+/* Per-image statistics of the last execution (synchronises `stream`). */
+int ctv_plan_stats(const ctv_plan* plan, ctv_stats* stats_host, ctv_stream stream);
+/* Configuration used, kernel launches per execution, pixel-iterations per
+ * execution and device bytes held; any pointer may be NULL. */
+int ctv_plan_info(const ctv_plan* plan, int* config, int* launches_per_execute, double* pixel_iters,
+                  size_t* device_bytes);
+void ctv_plan_destroy(ctv_plan* plan);
+
+/* --------------------------------------------------------------------------
+ * Phase retrieval, problem (24): min 1/2 || |A x| - sqrt(y) ||^2 + tau TV(x) + I_C(x),
+ * with A = crop o IFFT2 o (H *) o FFT2 o pad on an M x N grid (Eq. (23) when
+ * M = m and N = n; the object sits in the top-left m x n corner).
+ * A plan owns the cuFFT plan and its device buffers (about 3 M N complex64
+ * plus the FGP workspace); it is the only place the library allocates.
+ * sqrt_y: m x n float32, dense (row stride n). H: M x N complex64 transfer
+ * function (16-byte aligned). Images z, x, grad: m x n complex64, dense.
+ * One plan must not be used by two streams at the same time.
+ * -------------------------------------------------------------------------- */
+typedef struct ctv_pr_plan ctv_pr_plan;
+
+int ctv_pr_plan_create(int m, int n, int M, int N, ctv_pr_plan** out);
+void ctv_pr_plan_destroy(ctv_pr_plan* plan);
+
+/* grad = grad F(z) of Eq. (27) (A z / |A z| := 1 where A z = 0); loss: NULL or a
+ * DEVICE double receiving F(z) of Eq. (24). */
+int ctv_pr_gradient(ctv_pr_plan* plan, const void* z, const float* sqrt_y, const void* H,
+                    void* grad, double* loss, ctv_stream stream);
+
+/* Algorithm 1 (accelerate != 0; the gradient is taken at z_k) or ISTA, Eq. (14)
+ * (accelerate == 0), outer_iters iterations with step gamma. Each prox step is
+ * problem (15) with lambda = tau * gamma, solved by inner->max_iters iterations of
+ * Algorithm 2 (inner->alpha, inner->config used; gap stopping allowed), its dual
+ * warm-started from the previous outer iteration (t reset to 1).
+ * x_io: x_0 on entry, x_K on exit. loss_hist: NULL or DEVICE array of
+ * outer_iters doubles receiving F(z_k). */
+int ctv_pr_solve(ctv_pr_plan* plan, const float* sqrt_y, const void* H, float tau, float gamma,
+                 const ctv_constraint* C, int tv_type, const ctv_opts* inner, int outer_iters,
+                 int accelerate, void* x_io, double* loss_hist, ctv_stream stream);
+
+/* One proximal-gradient step for problem (2) with a caller-supplied gradient:
+ * v = z - gamma * grad; x_out = prox_{gamma (tau TV + I_C)}(v) by Algorithm 2
+ * (dual_state: NULL or the m x n float4 dual, warm start per inner->warm_start);
+ * z_next = x_out + beta (x_out - x_prev)  (Alg. 1, step 5 with
+ * beta = (t_k - 1)/t_{k+1}; beta = 0 gives ISTA, Eq. (14)).
+ * workspace: ctv_prox_grad_workspace_size(m, n) bytes. */
+size_t ctv_prox_grad_workspace_size(int m, int n);
+int ctv_prox_grad_step(const void* z, const void* grad, float gamma, float tau,
+                       const ctv_constraint* C, int tv_type, const ctv_opts* inner,
+                       void* dual_state, const void* x_prev, void* x_out, void* z_next,
+                       float beta, int m, int n, void* workspace, size_t workspace_bytes,
+                       ctv_stream stream);
+
+/* --------------------------------------------------------------------------
  * Measurement (no counterpart in the paper). ctv_profile_enable(1) resets the
  * counters and brackets every following launch of the fused FGP pass kernel
  * with CUDA events on its stream; ctv_profile_read synchronises on those events

@@ -42,6 +42,9 @@ class CtvImageDesc(C.Structure):
                 ("lam", c_float), ("alpha", c_float), ("tv_type", c_int), ("C", CtvConstraint)]
 
 
+assert C.sizeof(CtvConstraint) == 48 and C.sizeof(CtvOpts) == 32 and C.sizeof(CtvStats) == 40
+
+
 P = C.POINTER
 # name -> (restype, argtypes); every symbol include/ctv.h declares
 SIGNATURES = {
@@ -55,6 +58,20 @@ SIGNATURES = {
     "ctv_denoise_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_longlong, c_void_p,
                                     P(CtvConstraint), c_int, P(CtvOpts), c_void_p, c_void_p, c_size_t,
                                     P(CtvStats), c_void_p]),
+    "ctv_plan_create": (c_int, [c_void_p, c_int, P(CtvOpts), P(c_void_p)]),
+    "ctv_plan_execute": (c_int, [c_void_p, c_void_p]),
+    "ctv_plan_stats": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ctv_plan_info": (c_int, [c_void_p, P(c_int), P(c_int), P(c_double), P(c_size_t)]),
+    "ctv_plan_destroy": (None, [c_void_p]),
+    "ctv_pr_plan_create": (c_int, [c_int, c_int, c_int, c_int, P(c_void_p)]),
+    "ctv_pr_plan_destroy": (None, [c_void_p]),
+    "ctv_pr_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctv_pr_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, P(CtvConstraint), c_int,
+                             P(CtvOpts), c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "ctv_prox_grad_workspace_size": (c_size_t, [c_int, c_int]),
+    "ctv_prox_grad_step": (c_int, [c_void_p, c_void_p, c_float, c_float, P(CtvConstraint), c_int, P(CtvOpts),
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int, c_int, c_void_p,
+                                   c_size_t, c_void_p]),
     "ctv_profile_enable": (c_int, [c_int]),
     "ctv_profile_read": (c_int, [P(c_double), P(C.c_longlong), P(c_double), P(C.c_longlong)]),
 }

@@ -179,3 +179,150 @@ def configs():
         out.append({"config": i, "iters_per_pass": T.value, "region_w": W.value, "region_h": H.value,
                     "threads": NT.value})
     return out
+
+
+# ----------------------------------------------------------------------------- phase retrieval
+class PRPlan:
+    """cuFFT plan and device buffers for phase retrieval of an m x n object on an
+    M x N padded grid (C calls ctv_pr_plan_create / ctv_pr_plan_destroy)."""
+
+    def __init__(self, m: int, n: int, M: int, N: int):
+        self._lib = L.load()
+        h = C.c_void_p()
+        L.check("ctv_pr_plan_create", self._lib.ctv_pr_plan_create(m, n, M, N, C.byref(h)))
+        self.handle = h
+        self.m, self.n, self.M, self.N = m, n, M, N
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.ctv_pr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, z, sqrt_y, H):
+        _check_image(z, "z", 2)
+        if z.shape != (self.m, self.n) or not z.is_contiguous():
+            raise ValueError("z must be a contiguous (m, n) complex64 CUDA tensor")
+        if sqrt_y.shape != (self.m, self.n) or sqrt_y.dtype != torch.float32 or not sqrt_y.is_contiguous() \
+                or not sqrt_y.is_cuda:
+            raise ValueError("sqrt_y must be a contiguous (m, n) float32 CUDA tensor")
+        if H.shape != (self.M, self.N) or H.dtype != torch.complex64 or not H.is_contiguous() or not H.is_cuda:
+            raise ValueError("H must be a contiguous (M, N) complex64 CUDA tensor")
+
+    def gradient(self, z: torch.Tensor, sqrt_y: torch.Tensor, H: torch.Tensor, stream=None):
+        """grad F(z) of Eq. (27) and F(z) of Eq. (24) (ctv_pr_gradient)."""
+        self._check(z, sqrt_y, H)
+        g = torch.empty_like(z)
+        loss = torch.zeros(1, dtype=torch.float64, device=z.device)
+        L.check("ctv_pr_gradient", self._lib.ctv_pr_gradient(self.handle, z.data_ptr(), sqrt_y.data_ptr(),
+                                                             H.data_ptr(), g.data_ptr(), loss.data_ptr(),
+                                                             _stream_ptr(stream)))
+        return g, loss
+
+    def solve(self, x0: torch.Tensor, sqrt_y: torch.Tensor, H: torch.Tensor, tau: float, gamma: float = 1.0,
+              C: Optional[Constraint] = Constraint(), tv: Union[str, int] = "tv1_aniso", inner_iters: int = 10,
+              outer_iters: int = 300, alpha: float = 0.5, accelerate: bool = True, config: int = -1,
+              return_loss: bool = False, out: Optional[torch.Tensor] = None, stream=None):
+        """Algorithm 1 (or ISTA) from x0; returns x_K (and F(z_k) per outer iteration)."""
+        self._check(x0, sqrt_y, H)
+        x = out if out is not None else x0.clone()
+        if out is not None:
+            x.copy_(x0)
+        hist = torch.zeros(max(outer_iters, 1), dtype=torch.float64, device=x0.device) if return_loss else None
+        cc, keep = (C or NO_CONSTRAINT).to_c()
+        opts = make_opts(inner_iters, 0, 0.0, alpha, False, config)
+        L.check("ctv_pr_solve", self._lib.ctv_pr_solve(self.handle, sqrt_y.data_ptr(), H.data_ptr(), float(tau),
+                                                       float(gamma), C_ref(cc),
+                                                       tv_code(tv), C_ref(opts), int(outer_iters),
+                                                       int(bool(accelerate)), x.data_ptr(),
+                                                       hist.data_ptr() if hist is not None else None,
+                                                       _stream_ptr(stream)))
+        del keep
+        return (x, hist[:outer_iters]) if return_loss else x
+
+
+def ctv_prox_grad_step(z: torch.Tensor, grad: torch.Tensor, gamma: float, tau: float, C: Optional[Constraint],
+                       tv_type, opts: L.CtvOpts, dual_state: Optional[torch.Tensor], x_prev: torch.Tensor,
+                       x_out: torch.Tensor, z_next: torch.Tensor, beta: float, stream=None):
+    """One proximal-gradient step of problem (2) with a caller-supplied gradient
+    (C call ctv_prox_grad_step)."""
+    lib = L.load()
+    for t, nm in ((z, "z"), (grad, "grad"), (x_prev, "x_prev"), (x_out, "x_out"), (z_next, "z_next")):
+        _check_image(t, nm, 2)
+        if not t.is_contiguous() or t.shape != z.shape:
+            raise ValueError("%s must be contiguous with z's shape" % nm)
+    m, n = z.shape
+    ws = torch.empty(max(int(lib.ctv_prox_grad_workspace_size(m, n)), 256), dtype=torch.uint8, device=z.device)
+    cc, keep = (C or NO_CONSTRAINT).to_c()
+    L.check("ctv_prox_grad_step", lib.ctv_prox_grad_step(
+        z.data_ptr(), grad.data_ptr(), float(gamma), float(tau), C_ref(cc), tv_code(tv_type), C_ref(opts),
+        dual_state.data_ptr() if dual_state is not None else None, x_prev.data_ptr(), x_out.data_ptr(),
+        z_next.data_ptr(), float(beta), m, n, ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
+    del keep
+
+
+# ----------------------------------------------------------------------------- batched plans
+class Plan:
+    """Batched denoising of images of uneven sizes in one graph replay
+    (C calls ctv_plan_create / ctv_plan_execute / ctv_plan_stats).
+
+    images: sequence of dicts with keys b (complex64 CUDA (m, n)), x (output,
+    same shape and row stride), lam, and optionally tv, alpha, C."""
+
+    def __init__(self, images: Sequence[dict], iters: int, check_every: int = 0, gap_tol: float = 0.0,
+                 config: int = -1):
+        self._lib = L.load()
+        n = len(images)
+        arr = (L.CtvImageDesc * n)()
+        self._keep = []
+        for i, im in enumerate(images):
+            b, x = im["b"], im["x"]
+            _check_image(b, "b", 2)
+            _check_image(x, "x", 2)
+            if x.shape != b.shape or x.stride(0) != b.stride(0):
+                raise ValueError("x must have b's shape and row stride")
+            d = arr[i]
+            d.b, d.x = b.data_ptr(), x.data_ptr()
+            d.m, d.n, d.ld = b.shape[0], b.shape[1], b.stride(0)
+            d.lam = float(im["lam"])
+            d.alpha = float(im.get("alpha", 0.5))
+            d.tv_type = tv_code(im.get("tv", "tv1_iso"))
+            cc, keep = (im.get("C", Constraint()) or NO_CONSTRAINT).to_c()
+            d.C = cc
+            self._keep += [b, x, keep]
+        opts = make_opts(iters, check_every, gap_tol, 0.5, False, config)
+        h = C.c_void_p()
+        L.check("ctv_plan_create", self._lib.ctv_plan_create(arr, n, C.byref(opts), C.byref(h)))
+        self.handle = h
+        self.count = n
+
+    def execute(self, stream=None):
+        L.check("ctv_plan_execute", self._lib.ctv_plan_execute(self.handle, _stream_ptr(stream)))
+
+    def stats(self, stream=None):
+        st = (L.CtvStats * self.count)()
+        L.check("ctv_plan_stats", self._lib.ctv_plan_stats(self.handle, st, _stream_ptr(stream)))
+        return [s.as_dict() for s in st]
+
+    def info(self):
+        cfg, nl, pi, nb = C.c_int(), C.c_int(), C.c_double(), C.c_size_t()
+        L.check("ctv_plan_info", self._lib.ctv_plan_info(self.handle, C.byref(cfg), C.byref(nl), C.byref(pi),
+                                                         C.byref(nb)))
+        return {"config": cfg.value, "launches_per_execute": nl.value, "pixel_iters": pi.value,
+                "device_bytes": nb.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.ctv_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

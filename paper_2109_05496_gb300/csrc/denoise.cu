@@ -86,125 +86,36 @@ struct GapParams {
   int final_call;
 };
 
-constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
-
-// Region of GAP_RW x GAP_RH pixels with a one-pixel halo; the interior of
-// (GAP_RW-2) x (GAP_RH-2) pixels is evaluated. x at a pixel needs q at the pixel,
-// above and to the left; the TV summand needs x below and to the right.
+// Grid front end of gap_tile: blockIdx.z is the image of an equally sized batch.
 template <int TV>
 __global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
-  constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
-  __shared__ float4 qs[R];
-  __shared__ float2 xs[R];
-  __shared__ double red[4 * (NT / 32)];
+  __shared__ float4 qs[GAP_RW * GAP_RH];
+  __shared__ float2 xs[GAP_RW * GAP_RH];
+  __shared__ double red[3 * (GAP_NT / 32)];
   __shared__ int last;
   const int z = blockIdx.z;
   DevStats* st = p.st + z;
   const int stopped = *(volatile int*)&st->stop;
   if (!p.final_call && stopped) return;
   const int set = stopped ? st->stop_set : p.default_set;
+  GapImg g;
+  g.b = p.b + z * p.b_stride;
+  g.ld = p.ld;
+  const bool zq = p.zero_q != 0 && !stopped;
   const float4* q = set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in);
-  q += z * p.d_stride;
-  const float2* b = p.b + z * p.b_stride;
+  g.q = zq ? nullptr : q + z * p.d_stride;
+  g.x = p.x != nullptr ? p.x + z * p.x_stride : nullptr;
+  g.q_export = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
+  g.m = p.m;
+  g.n = p.n;
   float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
   const bool bad_lam = !(lam >= 0.f);
-  if (bad_lam) lam = 0.f;
-  const int m = p.m, n = p.n;
-  const int gj0 = blockIdx.y * (RH - 2) - 1, gk0 = blockIdx.x * (RW - 2) - 1;
-  const int tid = threadIdx.x;
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  const bool zq = p.zero_q != 0 && !stopped;
-
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
-    float4 v = z4;
-    if (!zq && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) v = __ldg(q + (long long)gj * n + gk);
-    qs[i] = v;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    float2 xv = make_float2(0.f, 0.f);
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 qc = qs[i];
-      const float4 qu = lj > 0 ? qs[i - RW] : z4;
-      const float4 ql = lk > 0 ? qs[i - 1] : z4;
-      const float2 bb = __ldg(b + (long long)gj * p.ld + gk);
-      xv = proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)),
-                  gj, gk, p.C);
-    }
-    xs[i] = xv;
-  }
-  __syncthreads();
-  double acc[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 qc = qs[i];
-      const float4 qu = qs[i - RW];
-      const float4 ql = qs[i - 1];
-      const float2 bb = __ldg(b + (long long)gj * p.ld + gk);
-      const float dlr = lam * (qc.x - qu.x + qc.z - ql.z);   // lam (L^T q)
-      const float dli = lam * (qc.y - qu.y + qc.w - ql.w);
-      const float wr = bb.x - dlr, wi = bb.y - dli;
-      const float2 xc = xs[i];
-      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-      if (gj < m - 1) { const float2 xd = xs[i + RW]; d1r = xc.x - xd.x; d1i = xc.y - xd.y; }
-      if (gk < n - 1) { const float2 xr = xs[i + 1]; d2r = xc.x - xr.x; d2i = xc.y - xr.y; }
-      const float er = xc.x - bb.x, ei = xc.y - bb.y;
-      acc[0] += (double)(er * er + ei * ei);
-      acc[1] += (double)tv_term<TV>(d1r, d1i, d2r, d2i, p.alpha);
-      // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
-      const float hr = wr - xc.x, hi = wi - xc.y;
-      acc[2] += (double)(2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (double)(hr * hr + hi * hi);
-      if (p.x != nullptr) p.x[z * p.x_stride + (long long)gj * p.ld + gk] = xc;
-      if (p.q_export != nullptr) p.q_export[z * p.d_stride + (long long)gj * n + gk] = qc;
-    }
-  }
-  block_sum<NT, 3>(acc, red);
-  if (tid == 0) {
-    atomicAdd(&st->acc[0], acc[0]);
-    atomicAdd(&st->acc[1], acc[1]);
-    atomicAdd(&st->acc[2], acc[2]);
-    __threadfence();
-    const unsigned nblk = gridDim.x * gridDim.y;
-    last = (atomicAdd(&st->blocks_done, 1u) == nblk - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (last && tid == 0) {
-    __threadfence();
-    volatile double* a = st->acc;
-    const double fid = a[0], tvs = a[1], dual2 = a[2];
-    const double P = 0.5 * fid + (double)lam * tvs;
-    const double D = 0.5 * dual2;
-    st->primal = P;
-    st->dual = D;
-    st->gap = P - D;
-    if (bad_lam) st->status = CTV_EINVAL;
-    if (!p.final_call) {
-      st->iters = p.iter;
-      if (p.gap_tol > 0.0 && P - D <= p.gap_tol * fmax(P, 1e-30)) {
-        st->stop = 1;
-        st->stop_set = set;
-        st->stop_iter = p.iter;
-      }
-    } else {
-      st->iters = stopped ? st->stop_iter : p.iter;
-    }
-    a[0] = 0.0;
-    a[1] = 0.0;
-    a[2] = 0.0;
-    __threadfence();
-    st->blocks_done = 0u;
-  }
+  g.lam = bad_lam ? 0.f : lam;
+  g.alpha = p.alpha;
+  g.C = p.C;
+  double acc[3];
+  gap_tile<TV>(g, blockIdx.y * (GAP_RH - 2), blockIdx.x * (GAP_RW - 2), qs, xs, red, acc);
+  gap_commit(st, acc, gridDim.x * gridDim.y, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
 }
 
 // ----------------------------------------------------------------------------

@@ -1,0 +1,393 @@
+// Batched denoising of many images of uneven sizes in one launch per pass.
+//
+// A plan holds, in one device allocation, a descriptor per image (its own m, n,
+// lambda, alpha, TV type, C and dual buffers) and two work lists of tiles over
+// all images: one for the fused FGP pass, one for the gap / finalize
+// evaluation. Each pass of Algorithm 2 is then a single launch whose blocks each
+// take one tile of one image (the TV type is chosen per block), so small images
+// no longer pay a launch each. The whole schedule (zeroing of the per-image
+// records, the passes, the optional gap checks and the finalize) is captured
+// once into a CUDA graph on a private stream and replayed on the caller's stream
+// by ctv_plan_execute. Every image keeps its own stopping test.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ctv.h"
+#include "ctv_device.cuh"
+#include "ctv_host.h"
+
+namespace ctv {
+
+struct PlanImg {
+  const float2* b;
+  float2* x;
+  int ld;
+  int m, n;
+  float lam, alpha;
+  int tv;
+  ConsDev C;
+  float4* q[2];
+  float4* r[2];
+  DevStats* st;
+  int tiles_x;     // pass tiles per tile row
+  int gtiles_x;    // gap tiles per tile row
+  unsigned gnblk;  // gap blocks of this image
+};
+
+struct WorkItem {
+  int img;
+  int tile;
+};
+
+struct ListPassParams {
+  const PlanImg* imgs;
+  const WorkItem* items;
+  int in_set;
+  int out_set;
+  int first;
+  int nsteps;
+  float beta[8];
+};
+
+template <int T, int RW, int RH, int NT>
+__global__ void __launch_bounds__(NT) fgp_pass_list_kernel(ListPassParams p) {
+  const WorkItem w = p.items[blockIdx.x];
+  const PlanImg d = p.imgs[w.img];
+  if (*(volatile const int*)&d.st->stop) return;
+  Img I;
+  I.b = d.b;
+  I.ld = d.ld;
+  I.q_in = d.q[p.in_set];
+  I.r_in = d.r[p.in_set];
+  I.q_out = d.q[p.out_set];
+  I.r_out = d.r[p.out_set];
+  I.m = d.m;
+  I.n = d.n;
+  I.lam = d.lam;
+  I.alpha = d.alpha;
+  I.C = d.C;
+  const int j0 = (w.tile / d.tiles_x) * (RH - 2 * T), k0 = (w.tile % d.tiles_x) * (RW - 2 * T);
+  const bool first = p.first != 0;
+  switch (d.tv) {
+    case TV1_ISO: fgp_tile<TV1_ISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
+    case TV1_ANISO: fgp_tile<TV1_ANISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
+    case TV2_ISO: fgp_tile<TV2_ISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
+    default: fgp_tile<TV2_ANISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
+  }
+}
+
+struct ListGapParams {
+  const PlanImg* imgs;
+  const WorkItem* items;
+  int default_set;
+  int zero_q;
+  int iter;
+  double gap_tol;
+  int final_call;
+};
+
+__global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
+  __shared__ float4 qs[GAP_RW * GAP_RH];
+  __shared__ float2 xs[GAP_RW * GAP_RH];
+  __shared__ double red[3 * (GAP_NT / 32)];
+  __shared__ int last;
+  const WorkItem w = p.items[blockIdx.x];
+  const PlanImg d = p.imgs[w.img];
+  const int stopped = *(volatile int*)&d.st->stop;
+  if (!p.final_call && stopped) return;
+  const int set = stopped ? d.st->stop_set : p.default_set;
+  GapImg g;
+  g.b = d.b;
+  g.ld = d.ld;
+  g.q = (p.zero_q && !stopped) ? nullptr : d.q[set];
+  g.x = p.final_call ? d.x : nullptr;
+  g.q_export = nullptr;
+  g.m = d.m;
+  g.n = d.n;
+  g.lam = d.lam;
+  g.alpha = d.alpha;
+  g.C = d.C;
+  const int j0 = (w.tile / d.gtiles_x) * (GAP_RH - 2), k0 = (w.tile % d.gtiles_x) * (GAP_RW - 2);
+  double acc[3];
+  switch (d.tv) {
+    case TV1_ISO: gap_tile<TV1_ISO>(g, j0, k0, qs, xs, red, acc); break;
+    case TV1_ANISO: gap_tile<TV1_ANISO>(g, j0, k0, qs, xs, red, acc); break;
+    case TV2_ISO: gap_tile<TV2_ISO>(g, j0, k0, qs, xs, red, acc); break;
+    default: gap_tile<TV2_ANISO>(g, j0, k0, qs, xs, red, acc); break;
+  }
+  gap_commit(d.st, acc, d.gnblk, d.lam, false, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+}
+
+template <int T, int RW, int RH, int NT>
+static cudaError_t launch_list_t(const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
+  constexpr size_t smem = (size_t)RW * RH * (sizeof(float4) + sizeof(float2));
+  if (set_attr) {
+    cudaError_t e = cudaFuncSetAttribute(fgp_pass_list_kernel<T, RW, RH, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  fgp_pass_list_kernel<T, RW, RH, NT><<<nblocks, NT, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_list(int cfg, const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
+  switch (cfg) {
+    case 0: return launch_list_t<1, 64, 16, 256>(p, nblocks, s, set_attr);
+    case 1: return launch_list_t<2, 64, 32, 256>(p, nblocks, s, set_attr);
+    case 2: return launch_list_t<4, 64, 32, 256>(p, nblocks, s, set_attr);
+    case 3: return launch_list_t<4, 64, 64, 512>(p, nblocks, s, set_attr);
+    case 4: return launch_list_t<8, 64, 64, 512>(p, nblocks, s, set_attr);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace ctv
+
+struct ctv_plan {
+  int count;
+  int K, check_every;
+  double gap_tol;
+  int cfg;
+  char* dev;
+  size_t bytes;
+  ctv::PlanImg* d_imgs;
+  ctv::WorkItem* d_pass;
+  int n_pass;
+  ctv::WorkItem* d_gap;
+  int n_gap;
+  ctv::DevStats* d_st;
+  std::vector<double> beta;
+  cudaStream_t cap;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int launches_per_execute;
+  double pixel_iters;
+};
+
+namespace ctv {
+
+static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
+  if (cudaMemsetAsync(P->d_st, 0, sizeof(DevStats) * (size_t)P->count, s) != cudaSuccess) return CTV_ECUDA;
+  int launches = 0;
+  int last_set = -1;
+  int T = 1;
+  config_info(P->cfg, &T, nullptr, nullptr, nullptr);
+  const int K = P->K, every = P->check_every;
+  ListGapParams g;
+  memset(&g, 0, sizeof(g));
+  g.imgs = P->d_imgs;
+  g.items = P->d_gap;
+  g.gap_tol = P->gap_tol;
+  if (K > 0) {
+    ListPassParams p;
+    memset(&p, 0, sizeof(p));
+    p.imgs = P->d_imgs;
+    p.items = P->d_pass;
+    int k = 1, out = 0;
+    bool first = true;
+    while (k <= K) {
+      int steps = std::min(T, K - k + 1);
+      if (every > 0) steps = std::min(steps, every - ((k - 1) % every));
+      for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)P->beta[(size_t)k + i] : 0.f;
+      p.nsteps = steps;
+      p.first = first ? 1 : 0;
+      p.in_set = out ^ 1;
+      p.out_set = out;
+      if (launch_list(P->cfg, p, P->n_pass, s, false) != cudaSuccess) return CTV_ECUDA;
+      ++launches;
+      first = false;
+      k += steps;
+      last_set = out;
+      out ^= 1;
+      if (every > 0 && (k - 1) % every == 0 && k - 1 < K) {
+        g.default_set = last_set;
+        g.zero_q = 0;
+        g.iter = k - 1;
+        g.final_call = 0;
+        fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
+        if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
+        ++launches;
+      }
+    }
+  }
+  g.default_set = last_set >= 0 ? last_set : 0;
+  g.zero_q = last_set < 0 ? 1 : 0;
+  g.iter = K;
+  g.final_call = 1;
+  fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
+  if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
+  ++launches;
+  P->launches_per_execute = launches;
+  return CTV_OK;
+}
+
+}  // namespace ctv
+
+extern "C" {
+
+int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts, ctv_plan** out) {
+  using namespace ctv;
+  if (out == nullptr) return CTV_EINVAL;
+  *out = nullptr;
+  if (descs == nullptr || count <= 0 || opts == nullptr) return CTV_EINVAL;
+  if (opts->max_iters < 0 || opts->check_every < 0 || !(opts->gap_tol >= 0.0) || opts->warm_start) return CTV_EINVAL;
+  int cfg = opts->config;
+  if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
+  if (cfg < 0) cfg = default_config(0, 0, opts->max_iters);
+  int T = 1, RW = 0, RH = 0, NT = 0;
+  config_info(cfg, &T, &RW, &RH, &NT);
+  const int TW = RW - 2 * T, TH = RH - 2 * T;
+  const int GW = GAP_RW - 2, GH = GAP_RH - 2;
+
+  std::vector<PlanImg> imgs((size_t)count);
+  std::vector<WorkItem> pass_items, gap_items;
+  size_t state_bytes = 0;
+  double px_total = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const ctv_image_desc& d = descs[i];
+    if (d.b == nullptr || d.x == nullptr || d.m <= 0 || d.n <= 0 || d.ld < d.n) return CTV_EINVAL;
+    if (((uintptr_t)d.b & 7) || ((uintptr_t)d.x & 7)) return CTV_EINVAL;
+    if (!(d.lambda >= 0.f) || isinf(d.lambda) || d.tv_type < 0 || d.tv_type > 3) return CTV_EINVAL;
+    if (!(d.alpha >= 0.f && d.alpha <= 1.f)) return CTV_EINVAL;
+    PlanImg& p = imgs[(size_t)i];
+    memset(&p, 0, sizeof(p));
+    if (!convert_constraint(&d.C, d.m, d.n, &p.C)) return CTV_EINVAL;
+    p.b = (const float2*)d.b;
+    p.x = (float2*)d.x;
+    p.ld = d.ld;
+    p.m = d.m;
+    p.n = d.n;
+    p.lam = d.lambda;
+    p.alpha = d.alpha;
+    p.tv = d.tv_type;
+    p.tiles_x = (d.n + TW - 1) / TW;
+    const int tiles_y = (d.m + TH - 1) / TH;
+    p.gtiles_x = (d.n + GW - 1) / GW;
+    const int gtiles_y = (d.m + GH - 1) / GH;
+    p.gnblk = (unsigned)(p.gtiles_x * gtiles_y);
+    for (int t = 0; t < p.tiles_x * tiles_y; ++t) pass_items.push_back({i, t});
+    for (int t = 0; t < (int)p.gnblk; ++t) gap_items.push_back({i, t});
+    state_bytes += 4 * a256((size_t)d.m * d.n * sizeof(float4));
+    px_total += (double)d.m * d.n;
+  }
+  if (pass_items.size() > 0x7fffffffu || gap_items.size() > 0x7fffffffu) return CTV_EINVAL;
+
+  ctv_plan* P = new ctv_plan();
+  P->count = count;
+  P->K = opts->max_iters;
+  P->check_every = opts->check_every;
+  P->gap_tol = opts->gap_tol;
+  P->cfg = cfg;
+  P->n_pass = (int)pass_items.size();
+  P->n_gap = (int)gap_items.size();
+  P->pixel_iters = px_total * P->K;
+  nesterov_betas(P->K, &P->beta);
+  const size_t b_imgs = a256(sizeof(PlanImg) * (size_t)count);
+  const size_t b_pass = a256(sizeof(WorkItem) * pass_items.size());
+  const size_t b_gap = a256(sizeof(WorkItem) * gap_items.size());
+  const size_t b_st = a256(sizeof(DevStats) * (size_t)count);
+  P->bytes = b_imgs + b_pass + b_gap + b_st + state_bytes;
+  if (cudaMalloc(&P->dev, P->bytes) != cudaSuccess) {
+    delete P;
+    return CTV_ENOMEM;
+  }
+  char* c = P->dev;
+  P->d_imgs = (PlanImg*)c; c += b_imgs;
+  P->d_pass = (WorkItem*)c; c += b_pass;
+  P->d_gap = (WorkItem*)c; c += b_gap;
+  P->d_st = (DevStats*)c; c += b_st;
+  for (int i = 0; i < count; ++i) {
+    PlanImg& p = imgs[(size_t)i];
+    const size_t db = a256((size_t)p.m * p.n * sizeof(float4));
+    p.q[0] = (float4*)c; c += db;
+    p.r[0] = (float4*)c; c += db;
+    p.q[1] = (float4*)c; c += db;
+    p.r[1] = (float4*)c; c += db;
+    p.st = P->d_st + i;
+  }
+  bool ok = cudaMemcpy(P->d_imgs, imgs.data(), sizeof(PlanImg) * (size_t)count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(P->d_pass, pass_items.data(), sizeof(WorkItem) * pass_items.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(P->d_gap, gap_items.data(), sizeof(WorkItem) * gap_items.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ListPassParams dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  ok = ok && launch_list(cfg, dummy, 0, nullptr, true) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaFree(P->dev);
+    delete P;
+    return CTV_ECUDA;
+  }
+  // capture the schedule once
+  if (cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaStreamDestroy(P->cap);
+    cudaFree(P->dev);
+    delete P;
+    return CTV_ECUDA;
+  }
+  ctv_status st = plan_enqueue(P, P->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(P->cap, &graph);
+  if (st != CTV_OK || ce != cudaSuccess || graph == nullptr ||
+      cudaGraphInstantiate(&P->exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(P->cap);
+    cudaFree(P->dev);
+    delete P;
+    return CTV_ECUDA;
+  }
+  P->graph = graph;
+  *out = P;
+  return CTV_OK;
+}
+
+int ctv_plan_execute(ctv_plan* P, ctv_stream stream) {
+  if (P == nullptr) return CTV_EINVAL;
+  if (cudaGraphLaunch(P->exec, (cudaStream_t)stream) != cudaSuccess) return CTV_ECUDA;
+  for (int i = 0; i < P->launches_per_execute; ++i) ctv::count_launch();
+  return CTV_OK;
+}
+
+int ctv_plan_stats(const ctv_plan* P, ctv_stats* out, ctv_stream stream) {
+  if (P == nullptr || out == nullptr) return CTV_EINVAL;
+  std::vector<ctv::DevStats> hs((size_t)P->count);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(hs.data(), P->d_st, sizeof(ctv::DevStats) * hs.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CTV_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CTV_ECUDA;
+  for (int i = 0; i < P->count; ++i) {
+    out[i].iters = hs[(size_t)i].iters;
+    out[i].stopped = hs[(size_t)i].stop;
+    out[i].primal = hs[(size_t)i].primal;
+    out[i].dual = hs[(size_t)i].dual;
+    out[i].gap = hs[(size_t)i].gap;
+    out[i].status = hs[(size_t)i].status;
+  }
+  return CTV_OK;
+}
+
+int ctv_plan_info(const ctv_plan* P, int* config, int* launches_per_execute, double* pixel_iters, size_t* device_bytes) {
+  if (P == nullptr) return CTV_EINVAL;
+  if (config) *config = P->cfg;
+  if (launches_per_execute) *launches_per_execute = P->launches_per_execute;
+  if (pixel_iters) *pixel_iters = P->pixel_iters;
+  if (device_bytes) *device_bytes = P->bytes;
+  return CTV_OK;
+}
+
+void ctv_plan_destroy(ctv_plan* P) {
+  if (P == nullptr) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  cudaFree(P->dev);
+  delete P;
+}
+
+}  // extern "C"

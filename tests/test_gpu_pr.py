@@ -1,0 +1,139 @@
+"""GPU parity of phase retrieval (Eq. (23), (24), (27), Algorithm 1 / Eq. (14))
+against the FP64 oracle after the same number of outer and inner iterations.
+
+Bar: max|x_gpu - x_oracle| <= 1e-4 ||x_0||_inf, gradients within 1e-4 of the
+largest gradient entry, F(z) within 1e-5 relative (cuFFT works in FP32)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2109_05496_gb300 as ctv
+from oracle import pr as opr
+from oracle.fgp import fgp
+from oracle.ops import Constraint as OC
+from phantoms import angular_spectrum_tf, fresnel_tf, pr_object, simulate_intensity
+from tests.helpers import f32
+
+pytestmark = pytest.mark.gpu
+
+CT = torch.complex128
+
+
+def problem(m, n, M, N, seed=3, kind="fresnel", photons=1e4):
+    if kind == "fresnel":
+        H = fresnel_tf(M, N, 532e-9, 2e-6, 5e-3)
+    else:
+        H = angular_spectrum_tf(M, N, 500e-9, 5e-6, 5e-3)
+    H = H.astype(np.complex64)
+    x_gt = pr_object(m, n, seed=seed, blur_sigma=max(1.0, m / 32))
+    y = simulate_intensity(x_gt, H.astype(np.complex128), seed=seed + 1, photons=photons)
+    sqrt_y = np.sqrt(y).astype(np.float32)
+    # x_0 = A^* sqrt(y), the back-propagated field, computed by the oracle in FP64
+    x0 = opr.propagate_adjoint(torch.tensor(sqrt_y.astype(np.float64)).to(CT), torch.tensor(H.astype(np.complex128)))
+    x0 = x0.numpy().astype(np.complex64)
+    return H, sqrt_y, x0, x_gt
+
+
+def to_gpu(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 128, 128), (48, 40, 96, 80), (33, 45, 33, 45)])
+def test_gradient_matches_oracle(shape):
+    m, n, M, N = shape
+    H, sqrt_y, x0, _ = problem(m, n, M, N)
+    rng = np.random.default_rng(1)
+    z = (x0 + 0.05 * (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))).astype(np.complex64)
+    plan = ctv.PRPlan(m, n, M, N)
+    zg, yg, Hg = to_gpu(z, sqrt_y, H)
+    g, loss = plan.gradient(zg, yg, Hg)
+    torch.cuda.synchronize()
+    Ht = torch.tensor(H.astype(np.complex128))
+    zt = torch.tensor(z.astype(np.complex128))
+    yt = torch.tensor(sqrt_y.astype(np.float64))
+    go = opr.fidelity_grad(zt, yt, Ht).numpy()
+    Fo = opr.fidelity(zt, yt, Ht)
+    err = np.abs(g.cpu().numpy() - go).max()
+    assert err <= 1e-4 * np.abs(go).max()
+    assert float(loss) == pytest.approx(Fo, rel=1e-5)
+
+
+@pytest.mark.parametrize("tv", ["tv1_aniso", "tv1_iso", "tv2_iso", "tv2_aniso"])
+@pytest.mark.parametrize("accelerate", [True, False])
+def test_solve_matches_oracle(tv, accelerate):
+    m, n, M, N = 48, 40, 96, 80
+    H, sqrt_y, x0, _ = problem(m, n, M, N, seed=7)
+    tau, gamma, K, inner = 0.01, 1.0, 12, 10
+    plan = ctv.PRPlan(m, n, M, N)
+    x0g, yg, Hg = to_gpu(x0, sqrt_y, H)
+    xg, hist = plan.solve(x0g, yg, Hg, tau, gamma, ctv.Constraint(amp_max=1.0), tv, inner, K,
+                          accelerate=accelerate, return_loss=True)
+    torch.cuda.synchronize()
+    xo, losses = opr.fista_pr(x0.astype(np.complex128), sqrt_y.astype(np.float64), H.astype(np.complex128),
+                              f32(tau), gamma, K, inner, tv, 0.5, OC(amp_max=1.0), accelerate=accelerate,
+                              record_loss=True)
+    err = np.abs(xg.cpu().numpy() - xo.numpy()).max()
+    assert err <= 1e-4 * np.abs(x0).max(), err
+    np.testing.assert_allclose(hist.cpu().numpy(), np.array(losses), rtol=1e-4)
+
+
+def test_solve_unpadded_angular_spectrum():
+    # M = m, N = n: A is Eq. (23) itself (no padding), with the angular-spectrum transfer function
+    m = n = 64
+    H, sqrt_y, x0, _ = problem(m, n, m, n, seed=9, kind="angular")
+    plan = ctv.PRPlan(m, n, m, n)
+    x0g, yg, Hg = to_gpu(x0, sqrt_y, H)
+    xg = plan.solve(x0g, yg, Hg, 0.02, 1.0, ctv.Constraint(amp_max=1.0), "tv1_aniso", 10, 10)
+    torch.cuda.synchronize()
+    xo, _ = opr.fista_pr(x0.astype(np.complex128), sqrt_y.astype(np.float64), H.astype(np.complex128),
+                         f32(0.02), 1.0, 10, 10, "tv1_aniso", 0.5, OC(amp_max=1.0))
+    assert np.abs(xg.cpu().numpy() - xo.numpy()).max() <= 1e-4 * np.abs(x0).max()
+
+
+def test_prox_grad_step_matches_oracle():
+    m, n = 50, 70
+    rng = np.random.default_rng(4)
+    z = (0.8 * np.exp(1j * rng.uniform(0, 3, (m, n)))).astype(np.complex64)
+    grad = (0.1 * (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))).astype(np.complex64)
+    xp = (0.7 * np.exp(1j * rng.uniform(0, 3, (m, n)))).astype(np.complex64)
+    gamma, tau, beta = 0.9, 0.03, 0.4
+    zg, gg, xpg = to_gpu(z, grad, xp)
+    xo_g = torch.empty_like(zg)
+    zn_g = torch.empty_like(zg)
+    opts = ctv.make_opts(15, alpha=0.5)
+    ctv.ctv_prox_grad_step(zg, gg, gamma, tau, ctv.Constraint(amp_max=1.0), "tv2_iso", opts, None, xpg,
+                           xo_g, zn_g, beta)
+    torch.cuda.synchronize()
+    v = z.astype(np.complex128) - np.float32(gamma) * grad.astype(np.complex128)
+    v = v.astype(np.complex64).astype(np.complex128)
+    vt = torch.tensor(v)
+    res = fgp((vt.real.clone(), vt.imag.clone()), f32(tau) * f32(gamma), 15, "tv2_iso", 0.5, OC(amp_max=1.0))
+    xo = (res.x[0] + 1j * res.x[1]).numpy()
+    zo = xo + f32(beta) * (xo - xp.astype(np.complex128))
+    assert np.abs(xo_g.cpu().numpy() - xo).max() <= 1e-4 * np.abs(v).max()
+    assert np.abs(zn_g.cpu().numpy() - zo).max() <= 2e-4 * np.abs(v).max()
+
+
+def test_full_size_first_iterations_and_convergence():
+    # the phase-retrieval workload: 1024^2 object, Fresnel TF (532 nm, 2 um, 5 mm), 2x padding,
+    # Poisson noise at 1e4 photons; first two outer iterations element by element, then a
+    # 300 x 10 run checked by its loss history and constraint
+    m = n = 1024
+    M = N = 2048
+    H, sqrt_y, x0, x_gt = problem(m, n, M, N, seed=11)
+    plan = ctv.PRPlan(m, n, M, N)
+    x0g, yg, Hg = to_gpu(x0, sqrt_y, H)
+    C = ctv.Constraint(amp_max=1.0)
+    xg = plan.solve(x0g, yg, Hg, 0.01, 1.0, C, "tv1_aniso", 10, 2)
+    torch.cuda.synchronize()
+    xo, _ = opr.fista_pr(x0.astype(np.complex128), sqrt_y.astype(np.float64), H.astype(np.complex128),
+                         f32(0.01), 1.0, 2, 10, "tv1_aniso", 0.5, OC(amp_max=1.0))
+    assert np.abs(xg.cpu().numpy() - xo.numpy()).max() <= 1e-4 * np.abs(x0).max()
+    xg, hist = plan.solve(x0g, yg, Hg, 0.01, 1.0, C, "tv1_aniso", 10, 300, return_loss=True)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    assert np.all(np.isfinite(h))
+    assert h[-1] < 0.2 * h[0]
+    assert float(xg.abs().max()) <= 1 + 1e-6
