@@ -54,7 +54,8 @@ typedef enum {
   CTV_ECUDA = 3,       /* a CUDA runtime or cuFFT call failed */
   CTV_ETIMEOUT = 4,    /* reserved: a bounded device wait ran out */
   CTV_ENONFINITE = 5,  /* reserved: non-finite input detected */
-  CTV_EUNSUPPORTED = 6 /* valid request that this build does not implement */
+  CTV_EUNSUPPORTED = 6, /* valid request that this build does not implement */
+  CTV_ETOOBIG = 7       /* image larger than the fixed scratch of ctv_denoise_noalloc */
 } ctv_status;
 
 /* The four complex TV seminorms: Eq. (7) type-I isotropic, Eq. (8) type-I
@@ -140,6 +141,32 @@ int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
                         const ctv_constraint* C, int tv_type, const ctv_opts* opts,
                         void* dual_state, void* workspace, size_t workspace_bytes,
                         ctv_stats* stats, ctv_stream stream);
+
+/* --------------------------------------------------------------------------
+ * ctv_denoise without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory - programs
+ * whose device memory all belongs to their own pool allocator, plugin hosts
+ * whose callbacks must not allocate, latency-critical loops where a cudaMalloc
+ * (which can synchronise the device) is not acceptable. It takes the same
+ * arguments as ctv_denoise minus the dual state and the workspace: its scratch
+ * (statistics record and FGP dual buffers) is a fixed device array inside the
+ * library, sized for images of at most CTV_NOALLOC_MAX_PIXELS pixels (m * n;
+ * 16 MiB, held on every GPU that loads the library until the process exits).
+ * Larger images return CTV_ETOOBIG; opts->warm_start must be 0. It never calls
+ * cudaMalloc, cudaFree or any allocating routine.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - Every call uses the same array, which keeps the previous call's contents
+ *   (each call clears what must start at zero). Calls that overlap on the GPU -
+ *   on two streams, or from two host threads - race on it and give wrong
+ *   results: serialise them.
+ * -------------------------------------------------------------------------- */
+#define CTV_NOALLOC_MAX_PIXELS (512 * 512)
+
+int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lambda,
+                        const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                        ctv_stats* stats /* host, nullable */, ctv_stream stream);
 
 /* --------------------------------------------------------------------------
  * Batched denoising of many images of uneven sizes (problem (1) per image).

@@ -58,6 +58,8 @@ SIGNATURES = {
     "ctv_denoise_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_longlong, c_void_p,
                                     P(CtvConstraint), c_int, P(CtvOpts), c_void_p, c_void_p, c_size_t,
                                     P(CtvStats), c_void_p]),
+    "ctv_denoise_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, P(CtvConstraint), c_int,
+                                    P(CtvOpts), P(CtvStats), c_void_p]),
     "ctv_plan_create": (c_int, [c_void_p, c_int, P(CtvOpts), P(c_void_p)]),
     "ctv_plan_execute": (c_int, [c_void_p, c_void_p]),
     "ctv_plan_stats": (c_int, [c_void_p, c_void_p, c_void_p]),

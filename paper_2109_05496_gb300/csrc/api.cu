@@ -12,6 +12,7 @@ const char* ctv_status_string(int status) {
     case CTV_ETIMEOUT: return "bounded device wait ran out";
     case CTV_ENONFINITE: return "non-finite input";
     case CTV_EUNSUPPORTED: return "unsupported";
+    case CTV_ETOOBIG: return "image exceeds the fixed scratch of ctv_denoise_noalloc (CTV_NOALLOC_MAX_PIXELS)";
   }
   return "unknown status";
 }
