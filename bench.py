@@ -173,6 +173,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
+    ap.add_argument("--workload", default="denoise2048",
+                    choices=("denoise2048", "denoise256", "batched", "pr", "backward"),
+                    help="denoise2048 is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -183,6 +186,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload != "denoise2048":
+        return run_other_workload(args, world, rank, local)
 
     import numpy as np
     import torch
@@ -319,6 +324,193 @@ def default_config_id(lib) -> int:
     # the library picks config 2 (4 iterations per pass) for K >= 2; mirrored here for the report
     import ctypes
     return 2 if ITERS >= 2 else 0
+
+
+# ----------------------------------------------------------------------------- other workloads
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_other_workload(args, world, rank, local):
+    """Secondary measurements, one JSON line each (single GPU)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_05496_gb300 as ctv
+    from phantoms import (batch_params, batch_shapes, fresnel_tf, noisy_phantom, pr_object, simulate_intensity,
+                          to_c64)
+    dev = torch.device("cuda", local)
+    out = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
+           "workload": args.workload}
+    if args.workload == "denoise256":
+        # 256^2 phantom, sigma 0.1, lambda 0.05, |x| <= 1, TV1 iso, 100 iterations; plain calls and a CUDA graph
+        _, noisy = noisy_phantom(256, 256, 0.1, seed=1)
+        b = torch.from_numpy(to_c64(noisy)).to(dev)
+        x = torch.empty_like(b)
+        ws = ctv.workspace(1, 256, 256, dev)
+        C = ctv.Constraint(amp_max=1.0)
+        res = {}
+        for cfg in ([args.config] if args.config >= 0 else [0, 2, 4, 10, 11]):
+            opts = ctv.make_opts(100, config=cfg)
+            for _ in range(args.warmup):
+                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record()
+            for _ in range(args.steps):
+                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            plain_us = e0.elapsed_time(e1) * 1e3 / args.steps
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+            for _ in range(args.warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            graph_us = e0.elapsed_time(e1) * 1e3 / args.steps
+            res[cfg] = {"us_per_solve": plain_us, "us_per_solve_graph": graph_us,
+                        "gpx_it_s_graph": 256 * 256 * 100 / (graph_us * 1e-6) / 1e9}
+        best = min(res, key=lambda c: res[c]["us_per_solve_graph"])
+        out.update({"metric": "FGP 256x256 solve time (100 iterations)", "value": res[best]["us_per_solve_graph"],
+                    "unit": "us/solve", "higher_is_better": False, "configs": res, "best_config": best})
+    elif args.workload == "batched":
+        # 512 images, sides log-uniform in [64, 1024], lambda ~ U[0.01, 0.1], mixed TV, 100 iterations
+        shapes = batch_shapes(512, 64, 1024, seed=2021)
+        lams, types = batch_params(512, seed=2022)
+        tvs = ["tv1_iso", "tv1_aniso", "tv2_iso", "tv2_aniso"]
+        ims = []
+        for i, (m, n) in enumerate(shapes):
+            _, noisy = noisy_phantom(m, n, 0.1, seed=2021000 + i)
+            bb = torch.from_numpy(to_c64(noisy)).to(dev)
+            ims.append({"b": bb, "x": torch.empty_like(bb), "lam": float(lams[i]), "tv": tvs[int(types[i])],
+                        "alpha": 0.5, "C": ctv.Constraint(amp_max=1.0)})
+        cfg = args.config if args.config >= 0 else -1
+        plan = ctv.Plan(ims, 100, config=cfg)
+        info = plan.info()
+        for _ in range(args.warmup):
+            plan.execute()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(args.steps):
+            plan.execute()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_plan = e0.elapsed_time(e1) / args.steps
+        wss = {}
+        opts = ctv.make_opts(100, config=info["config"])
+        for im in ims:
+            key = tuple(im["b"].shape)
+            if key not in wss:
+                wss[key] = ctv.workspace(1, key[0], key[1], dev)
+
+        def loop():
+            for im in ims:
+                ctv.ctv_denoise(im["b"], im["x"], im["lam"], im["C"], im["tv"], opts, ws=wss[tuple(im["b"].shape)])
+
+        loop()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(max(1, args.steps // 3)):
+            loop()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1) / max(1, args.steps // 3)
+        pxit = info["pixel_iters"]
+        out.update({"metric": "batched FGP Gpixel-iter/s (512 uneven images, one graph replay) vs per-image loop",
+                    "value": pxit / (ms_plan * 1e-3) / 1e9, "unit": "Gpixel-iter/s", "higher_is_better": True,
+                    "ms_per_batch": ms_plan, "looped_ms_per_batch": ms_loop,
+                    "looped_value": pxit / (ms_loop * 1e-3) / 1e9, "speedup_vs_loop": ms_loop / ms_plan,
+                    "plan": info, "images": 512, "megapixels": pxit / 100 / 1e6})
+    elif args.workload == "pr":
+        # 1024^2 object, Fresnel TF (532 nm, 2 um, 5 mm), 2x padding, Poisson 1e4 photons, 300 x 10, tau 0.01
+        m = n = 1024
+        M = N = 2048
+        H = fresnel_tf(M, N, 532e-9, 2e-6, 5e-3).astype(np.complex64)
+        x_gt = pr_object(m, n, seed=11)
+        y = simulate_intensity(x_gt, H.astype(np.complex128), seed=12, photons=1e4)
+        sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
+        Hg = torch.from_numpy(H).to(dev)
+        plan = ctv.PRPlan(m, n, M, N)
+        x0 = torch.empty(m, n, dtype=torch.complex64, device=dev)
+        g, _ = plan.gradient(torch.zeros_like(x0), sqrt_y, Hg)
+        x0.copy_(-g)                    # A^* sqrt(y): the gradient at 0 is -A^*(sqrt(y))
+        outer = 300
+        C = ctv.Constraint(amp_max=1.0)
+        for _ in range(args.warmup):
+            plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, 10)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        xk, hist = plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer, return_loss=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        xg = xk.cpu().numpy()
+        ph = np.angle(xg * np.conj(x_gt))
+        ph = np.angle(np.exp(1j * (ph - np.angle(np.exp(1j * ph).mean()))))
+        ph0 = np.angle(x0.cpu().numpy() * np.conj(x_gt))
+        ph0 = np.angle(np.exp(1j * (ph0 - np.angle(np.exp(1j * ph0).mean()))))
+        h = hist.cpu().numpy()
+        out.update({"metric": "phase retrieval outer iterations/s (1024^2 object, 2048^2 FFTs, 10 FGP iterations each)",
+                    "value": outer / (ms * 1e-3), "unit": "outer-iter/s", "higher_is_better": True,
+                    "ms_total": ms, "fgp_pixel_iters": outer * 10 * m * n,
+                    "loss_first": float(h[0]), "loss_last": float(h[-1]),
+                    "phase_rmse_initial": float(np.sqrt((ph0 ** 2).mean())),
+                    "phase_rmse_final": float(np.sqrt((ph ** 2).mean()))})
+    elif args.workload == "backward":
+        # 8 x 1024^2, 50 unrolled iterations, checkpoints every 10, loss ||x - x_gt||^2
+        Bn, m, n, K = 8, 1024, 1024, 50
+        cl, nz = [], []
+        for i in range(Bn):
+            c_, z_ = noisy_phantom(m, n, 0.1, seed=700 + i)
+            cl.append(to_c64(c_))
+            nz.append(to_c64(z_))
+        b = torch.from_numpy(np.stack(nz)).to(dev).requires_grad_(True)
+        gt = torch.from_numpy(np.stack(cl)).to(dev)
+        lam = torch.linspace(0.02, 0.09, Bn, device=dev).requires_grad_(True)
+        C = ctv.Constraint(amp_max=1.0)
+        cfg = args.config if args.config >= 0 else -1
+
+        def fwd():
+            return ctv.denoise_unrolled(b, lam, "tv1_iso", K, C, 0.5, 10, cfg)
+
+        for _ in range(args.warmup):
+            loss = ((fwd() - gt).abs() ** 2).sum()
+            loss.backward()
+        torch.cuda.synchronize()
+        tf = tb = 0.0
+        for _ in range(args.steps):
+            e0, e1 = _events()
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x = fwd()
+            e1.record()
+            loss = ((x - gt).abs() ** 2).sum()
+            e3 = torch.cuda.Event(enable_timing=True)
+            e3.record()
+            loss.backward()
+            e2.record()
+            torch.cuda.synchronize()
+            tf += e0.elapsed_time(e1)
+            tb += e3.elapsed_time(e2)
+        tf /= args.steps
+        tb /= args.steps
+        out.update({"metric": "unrolled FGP backward/forward time ratio (8 x 1024^2, 50 iterations, ckpt 10)",
+                    "value": tb / tf, "unit": "ratio", "higher_is_better": False, "forward_ms": tf,
+                    "backward_ms": tb, "forward_gpx_it_s": Bn * m * n * K / (tf * 1e-3) / 1e9})
+    print(json.dumps(out))
 
 
 def run_reference(args, world, rank):

@@ -119,6 +119,23 @@ int ctv_abi_version(void);
 int ctv_num_configs(void);
 int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads);
 
+/* Autotuner (no counterpart in the paper). ctv_autotune_denoise runs
+ * ctv_denoise once per configuration plus `repeats` timed times on the caller's
+ * data (same arguments as ctv_denoise, the options' config, stopping and warm
+ * start ignored), writes x, synchronises `stream`, returns the fastest
+ * configuration in *best_config (times_ms: NULL or ctv_num_configs() floats) and
+ * records it for the image's size class and TV type, which then becomes the
+ * choice of every call with opts->config = -1. The size class of an m x n image
+ * is floor(log2(m n)); ctv_tune_get / ctv_tune_set read and write that table
+ * (-1: untuned) so that it can be saved and restored. */
+int ctv_size_class(int m, int n);
+int ctv_tune_get(int size_class, int tv_type, int* config);
+int ctv_tune_set(int size_class, int tv_type, int config);
+int ctv_autotune_denoise(const void* b, void* x, int m, int n, int ld, float lambda,
+                         const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                         void* workspace, size_t workspace_bytes, int repeats, int* best_config,
+                         float* times_ms, ctv_stream stream);
+
 /* --------------------------------------------------------------------------
  * Denoising, problem (1), by Algorithm 2.
  * b: input image(s); x: output x_K = P_C(b - lambda L^T(q_K)) (Eq. (18)).
@@ -199,6 +216,30 @@ int ctv_plan_stats(const ctv_plan* plan, ctv_stats* stats_host, ctv_stream strea
 int ctv_plan_info(const ctv_plan* plan, int* config, int* launches_per_execute, double* pixel_iters,
                   size_t* device_bytes);
 void ctv_plan_destroy(ctv_plan* plan);
+
+/* --------------------------------------------------------------------------
+ * Differentiation through K unrolled iterations of Algorithm 2 (no counterpart
+ * in the paper; the forward map is exactly ctv_denoise_batched with stopping
+ * off). A batch of `batch` dense m x n images (row stride n, image stride m n),
+ * per-image lambda in the DEVICE array lambdas (> 0 for a meaningful lambda
+ * gradient; lambda = 0 images get lambdabar = 0), opts->max_iters = K >= 1,
+ * opts->alpha, opts->config (a configuration the recompute supports, else the
+ * default); warm_start must be 0.
+ * ctv_unrolled_forward writes x = x_K and keeps the state every ckpt_every
+ * iterations in the workspace; ctv_unrolled_backward takes xbar = dL/dx and
+ * returns bbar = dL/db (complex64, same layout as b) and lambdabar = dL/dlambda
+ * (DEVICE float per image), recomputing each checkpoint segment. The workspace
+ * (ctv_unrolled_workspace_size bytes) must be the one the forward call used and
+ * must not be touched in between.
+ * -------------------------------------------------------------------------- */
+size_t ctv_unrolled_workspace_size(int batch, int m, int n, int iters, int ckpt_every);
+int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const float* lambdas,
+                         const ctv_constraint* C, int tv_type, const ctv_opts* opts, int ckpt_every,
+                         void* workspace, size_t workspace_bytes, ctv_stream stream);
+int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* lambdabar, int batch,
+                          int m, int n, const float* lambdas, const ctv_constraint* C, int tv_type,
+                          const ctv_opts* opts, int ckpt_every, void* workspace,
+                          size_t workspace_bytes, ctv_stream stream);
 
 /* --------------------------------------------------------------------------
  * Phase retrieval, problem (24): min 1/2 || |A x| - sqrt(y) ||^2 + tau TV(x) + I_C(x),

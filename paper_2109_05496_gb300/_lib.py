@@ -53,6 +53,11 @@ SIGNATURES = {
     "ctv_num_configs": (c_int, []),
     "ctv_config_info": (c_int, [c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
     "ctv_denoise_workspace_size": (c_size_t, [c_int, c_int, c_int]),
+    "ctv_size_class": (c_int, [c_int, c_int]),
+    "ctv_tune_get": (c_int, [c_int, c_int, P(c_int)]),
+    "ctv_tune_set": (c_int, [c_int, c_int, c_int]),
+    "ctv_autotune_denoise": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, P(CtvConstraint), c_int,
+                                     P(CtvOpts), c_void_p, c_size_t, c_int, P(c_int), c_void_p, c_void_p]),
     "ctv_denoise": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, P(CtvConstraint), c_int,
                             P(CtvOpts), c_void_p, c_void_p, c_size_t, P(CtvStats), c_void_p]),
     "ctv_denoise_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_longlong, c_void_p,
@@ -60,6 +65,11 @@ SIGNATURES = {
                                     P(CtvStats), c_void_p]),
     "ctv_denoise_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, P(CtvConstraint), c_int,
                                     P(CtvOpts), P(CtvStats), c_void_p]),
+    "ctv_unrolled_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "ctv_unrolled_forward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(CtvConstraint), c_int,
+                                     P(CtvOpts), c_int, c_void_p, c_size_t, c_void_p]),
+    "ctv_unrolled_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                      P(CtvConstraint), c_int, P(CtvOpts), c_int, c_void_p, c_size_t, c_void_p]),
     "ctv_plan_create": (c_int, [c_void_p, c_int, P(CtvOpts), P(c_void_p)]),
     "ctv_plan_execute": (c_int, [c_void_p, c_void_p]),
     "ctv_plan_stats": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -326,3 +326,67 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- differentiation
+def _unrolled_checks(b, lams):
+    _check_image(b, "b", 3)
+    if not b.is_contiguous():
+        raise ValueError("b must be contiguous (B, m, n)")
+    if not (lams.is_cuda and lams.dtype == torch.float32 and lams.numel() == b.shape[0] and lams.is_contiguous()):
+        raise ValueError("lams must be a contiguous CUDA float32 tensor with one value per image")
+
+
+class UnrolledFGP(torch.autograd.Function):
+    """x = K unrolled iterations of Algorithm 2 followed by Eq. (18), for a batch
+    (B, m, n) of complex64 images and per-image lambda, differentiable with
+    respect to b and lambda through the library's adjoint kernels (C calls
+    ctv_unrolled_forward / ctv_unrolled_backward). Gradients follow torch's
+    convention for real losses of complex tensors: dL/dRe + i dL/dIm."""
+
+    @staticmethod
+    def forward(ctx, b, lams, tv, iters, C, alpha, ckpt_every, config):
+        lib = L.load()
+        b = b.contiguous()
+        lams = lams.contiguous()
+        _unrolled_checks(b, lams)
+        B, m, n = b.shape
+        nbytes = int(lib.ctv_unrolled_workspace_size(B, m, n, int(iters), int(ckpt_every)))
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=b.device)
+        x = torch.empty_like(b)
+        cc, keep = (C or NO_CONSTRAINT).to_c()
+        opts = make_opts(iters, 0, 0.0, alpha, False, config)
+        L.check("ctv_unrolled_forward", lib.ctv_unrolled_forward(
+            b.data_ptr(), x.data_ptr(), B, m, n, lams.data_ptr(), C_ref(cc), tv_code(tv), C_ref(opts),
+            int(ckpt_every), ws.data_ptr(), ws.numel(), _stream_ptr()))
+        ctx.save_for_backward(b, lams)
+        ctx.ws, ctx.keep, ctx.cc, ctx.opts = ws, keep, cc, opts
+        ctx.meta = (tv_code(tv), int(ckpt_every))
+        return x
+
+    @staticmethod
+    def backward(ctx, xbar):
+        lib = L.load()
+        b, lams = ctx.saved_tensors
+        B, m, n = b.shape
+        xbar = xbar.to(torch.complex64).contiguous()
+        bbar = torch.empty_like(b)
+        lbar = torch.empty(B, dtype=torch.float32, device=b.device)
+        tv, ck = ctx.meta
+        L.check("ctv_unrolled_backward", lib.ctv_unrolled_backward(
+            b.data_ptr(), xbar.data_ptr(), bbar.data_ptr(), lbar.data_ptr(), B, m, n, lams.data_ptr(),
+            C_ref(ctx.cc), tv, C_ref(ctx.opts), ck, ctx.ws.data_ptr(), ctx.ws.numel(), _stream_ptr()))
+        return bbar, lbar, None, None, None, None, None, None
+
+
+def denoise_unrolled(b: torch.Tensor, lams, tv: Union[str, int] = "tv1_iso", iters: int = 50,
+                     C: Optional[Constraint] = Constraint(), alpha: float = 0.5, ckpt_every: int = 10,
+                     config: int = -1) -> torch.Tensor:
+    """Differentiable form of ``denoise`` for a batch (B, m, n) (or one (m, n) image)."""
+    squeeze = b.dim() == 2
+    bb = b.unsqueeze(0) if squeeze else b
+    if not isinstance(lams, torch.Tensor):
+        lams = torch.full((bb.shape[0],), float(lams), dtype=torch.float32, device=b.device)
+    lams = lams.to(device=b.device, dtype=torch.float32).reshape(-1)
+    x = UnrolledFGP.apply(bb, lams, tv, iters, C, alpha, ckpt_every, config)
+    return x.squeeze(0) if squeeze else x

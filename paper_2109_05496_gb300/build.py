@@ -26,6 +26,19 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
 
+def config_table():
+    """(id, kind, T, A, B, C) rows of the fused-pass configuration table in
+    csrc/ctv_configs.cuh (read from the source, so no GPU or built library is needed)."""
+    import re
+    rows = []
+    with open(os.path.join(CSRC, "ctv_configs.cuh")) as f:
+        for m in re.finditer(r"^\s*X\(([^)]*)\)", f.read(), flags=re.M):
+            vals = [v.strip() for v in m.group(1).split(",")]
+            if all(v.isdigit() for v in vals):
+                rows.append(tuple(int(v) for v in vals))
+    return rows
+
+
 def nvcc() -> str:
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):

@@ -1,0 +1,691 @@
+// Differentiation through K unrolled iterations of Algorithm 2.
+//
+// Forward (ctv_unrolled_forward): the fused FGP passes over an equally sized
+// batch, split at every ckpt_every iterations, where the state (q_k, r_{k+1}) is
+// kept as a checkpoint, followed by x = P_C(b - lam L^T q_K) (Eq. (18)).
+//
+// Backward (ctv_unrolled_backward), given xbar = dLoss/dx:
+//   finalize:   what = J_PC(w_K)^T xbar, w_K = b - lam L^T q_K;
+//               bbar = what, lambar = -<L^T q_K, what>, qbar_K = -lam L what
+//   step k = K..1 (forward map (q_{k-1}, r_k) -> (q_k, r_{k+1})):
+//     d = L^T r_k, w = b - lam d, x = P_C(w), e = L x, g = r_k + e / (8 lam)
+//     qbar_k = qbar-carry + (1 + beta_k) rbar_{k+1},  the carry being qbar_K at
+//              k = K and -beta_{k+1} rbar_{k+2} below it (r_{k+1} = (1+beta_k) q_k - beta_k q_{k-1})
+//     gbar = J_PS(g)^T qbar_k   (zero on the padded dual slots)
+//     ebar = gbar / (8 lam),  xbar_k = L^T ebar,  what = J_PC(w)^T xbar_k
+//     bbar += what,  lambar += -<gbar, e>/(8 lam^2) - <d, what>
+//     rbar_k = gbar - lam L what
+// Each segment of ckpt_every iterations is first recomputed from its
+// checkpoint by the fused pass, storing every r_k of the segment, then walked
+// backwards one reverse step per launch (a two-pixel halo: the reverse step
+// reads two stencils deep). All Jacobians are those of the projections, which
+// are symmetric; at a projection's boundary the interior branch (identity) is
+// taken, and the projection onto a radius-0 ball has Jacobian 0.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ctv.h"
+#include "ctv_configs.cuh"
+#include "ctv_device.cuh"
+#include "ctv_host.h"
+#include "ctv_kernels.h"
+
+namespace ctv {
+
+// xhat = J_PC(w)^T xbar
+__device__ __forceinline__ float2 proj_C_adj(float2 w, float2 xb, int gj, int gk, const ConsDev& c) {
+  if (c.sup == 1) {
+    if (gj < c.j0 || gj >= c.j1 || gk < c.k0 || gk >= c.k1) return make_float2(0.f, 0.f);
+  } else if (c.sup == 2) {
+    if (c.mask[(long long)gj * c.mask_ld + gk] == 0) return make_float2(0.f, 0.f);
+  }
+  if (c.amp) {
+    const float a2 = w.x * w.x + w.y * w.y;
+    if (a2 > c.amax * c.amax) {
+      const float inv = rsqrtf(a2);
+      const float nx = w.x * inv, ny = w.y * inv;
+      const float dot = nx * xb.x + ny * xb.y;
+      const float s = c.amax * inv;
+      return make_float2(s * (xb.x - nx * dot), s * (xb.y - ny * dot));
+    }
+  }
+  return xb;
+}
+
+// (a, b) <- J^T (a, b) for the projection of the pair (u, v) onto the ball of radius rad
+__device__ __forceinline__ void ball2_adj(float u, float v, float rad, float& a, float& b) {
+  if (rad <= 0.f) { a = 0.f; b = 0.f; return; }
+  const float nn = u * u + v * v;
+  if (nn > rad * rad) {
+    const float inv = rsqrtf(nn);
+    const float nu = u * inv, nv = v * inv;
+    const float dot = nu * a + nv * b;
+    const float s = rad * inv;
+    a = s * (a - nu * dot);
+    b = s * (b - nv * dot);
+  }
+}
+
+// gbar = J_PS(g)^T qbar for the four TV types; g = (r1, s1, r2, s2)
+template <int TV>
+__device__ __forceinline__ float4 proj_S_adj(float4 g, float4 qb, float alpha) {
+  if (TV == TV1_ISO) {
+    const float nn = g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w;
+    if (nn > 1.f) {
+      const float inv = rsqrtf(nn);
+      const float4 n = f4(g.x * inv, g.y * inv, g.z * inv, g.w * inv);
+      const float dot = n.x * qb.x + n.y * qb.y + n.z * qb.z + n.w * qb.w;
+      qb = f4(inv * (qb.x - n.x * dot), inv * (qb.y - n.y * dot), inv * (qb.z - n.z * dot), inv * (qb.w - n.w * dot));
+    }
+  } else if (TV == TV1_ANISO) {
+    ball2_adj(g.x, g.y, 1.f, qb.x, qb.y);
+    ball2_adj(g.z, g.w, 1.f, qb.z, qb.w);
+  } else if (TV == TV2_ISO) {
+    ball2_adj(g.x, g.z, alpha, qb.x, qb.z);
+    ball2_adj(g.y, g.w, 1.f - alpha, qb.y, qb.w);
+  } else {
+    const float a = alpha, c = 1.f - alpha;
+    if (a <= 0.f || g.x * g.x > a * a) qb.x = 0.f;
+    if (a <= 0.f || g.z * g.z > a * a) qb.z = 0.f;
+    if (c <= 0.f || g.y * g.y > c * c) qb.y = 0.f;
+    if (c <= 0.f || g.w * g.w > c * c) qb.w = 0.f;
+  }
+  return qb;
+}
+
+constexpr int ADJ_RW = 64, ADJ_RH = 24, ADJ_NT = 512;
+
+struct AdjParams {
+  const float2* b;        // dense m x n per image, image stride px
+  const float4* r;        // r_k (nullptr: 0)
+  const float4* Y;        // carry: qbar_K or rbar_{k+2} (nullptr: 0)
+  float yc;               // coefficient of Y
+  const float4* rbn;      // rbar_{k+1} (nullptr: 0)
+  float rc;               // 1 + beta_k
+  float4* rb_out;         // rbar_k
+  const float2* xbar;     // finalize only
+  const float4* qK;       // finalize only
+  float4* qbK;            // finalize only: qbar_K
+  float2* bbar;
+  double* lamacc;
+  long long px;
+  int m, n;
+  const float* lam_dev;
+  float alpha;
+  ConsDev C;
+};
+
+template <int TV>
+__global__ void __launch_bounds__(ADJ_NT) adj_step_kernel(AdjParams p) {
+  constexpr int RW = ADJ_RW, RH = ADJ_RH, NT = ADJ_NT, R = RW * RH, PPT = R / NT;
+  __shared__ float4 RE[R];   // r_k, then ebar
+  __shared__ float2 XW[R];   // x, then what
+  __shared__ double red[NT / 32];
+  const int z = blockIdx.z;
+  const long long off = (long long)z * p.px;
+  const float lam = fmaxf(p.lam_dev[z], 0.f);
+  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
+  const int m = p.m, n = p.n;
+  const int gj0 = blockIdx.y * (RH - 4) - 2, gk0 = blockIdx.x * (RW - 4) - 2;
+  const int tid = threadIdx.x;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  float2 bb[PPT], dd[PPT], ww[PPT];
+  float4 qb[PPT], gb[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
+    float4 r = z4, q = z4;
+    float2 b2 = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const long long o = off + (long long)gj * n + gk;
+      if (p.r != nullptr) r = __ldg(p.r + o);
+      b2 = __ldg(p.b + o);
+      if (p.Y != nullptr) {
+        const float4 y = __ldg(p.Y + o);
+        q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
+      }
+      if (p.rbn != nullptr) {
+        const float4 y = __ldg(p.rbn + o);
+        q = f4(q.x + p.rc * y.x, q.y + p.rc * y.y, q.z + p.rc * y.z, q.w + p.rc * y.w);
+      }
+    }
+    RE[i] = r;
+    bb[s] = b2;
+    qb[s] = q;
+  }
+  __syncthreads();
+  // A: d = L^T r, w = b - lam d, x = P_C(w)
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float2 xv = make_float2(0.f, 0.f);
+    dd[s] = make_float2(0.f, 0.f);
+    ww[s] = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float4 rc = RE[i];
+      const float4 ru = lj > 0 ? RE[i - RW] : z4;
+      const float4 rl = lk > 0 ? RE[i - 1] : z4;
+      dd[s] = make_float2(rc.x - ru.x + rc.z - rl.z, rc.y - ru.y + rc.w - rl.w);
+      ww[s] = make_float2(bb[s].x - lam * dd[s].x, bb[s].y - lam * dd[s].y);
+      xv = proj_C(ww[s], gj, gk, p.C);
+    }
+    XW[i] = xv;
+  }
+  __syncthreads();
+  // B: e = L x, g = r + e/(8 lam), gbar = J_PS(g)^T qbar, ebar = gbar/(8 lam)
+  double lacc = 0.0;
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float4 eb = z4;
+    gb[s] = z4;
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float2 xc = XW[i];
+      float e1r = 0.f, e1i = 0.f, e2r = 0.f, e2i = 0.f;
+      if (gj < m - 1 && lj < RH - 1) { const float2 xd = XW[i + RW]; e1r = xc.x - xd.x; e1i = xc.y - xd.y; }
+      if (gk < n - 1 && lk < RW - 1) { const float2 xr = XW[i + 1]; e2r = xc.x - xr.x; e2i = xc.y - xr.y; }
+      const float4 rc = RE[i];
+      const float4 g = f4(rc.x + c8 * e1r, rc.y + c8 * e1i, rc.z + c8 * e2r, rc.w + c8 * e2i);
+      float4 gbar = proj_S_adj<TV>(g, qb[s], p.alpha);
+      if (gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
+      if (gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
+      gb[s] = gbar;
+      eb = f4(c8 * gbar.x, c8 * gbar.y, c8 * gbar.z, c8 * gbar.w);
+      if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2)
+        lacc -= (double)(8.f * c8 * c8) * (double)(gbar.x * e1r + gbar.y * e1i + gbar.z * e2r + gbar.w * e2i);
+    }
+    RE[i] = eb;
+  }
+  __syncthreads();
+  // C: xbar = L^T ebar, what = J_PC(w)^T xbar; bbar += what
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float2 wh = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float4 ec = RE[i];
+      const float4 eu = lj > 0 ? RE[i - RW] : z4;
+      const float4 el = lk > 0 ? RE[i - 1] : z4;
+      const float2 xb = make_float2(ec.x - eu.x + ec.z - el.z, ec.y - eu.y + ec.w - el.w);
+      wh = proj_C_adj(ww[s], xb, gj, gk, p.C);
+      if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2) {
+        const long long o = off + (long long)gj * n + gk;
+        float2 acc = p.bbar[o];
+        acc.x += wh.x;
+        acc.y += wh.y;
+        p.bbar[o] = acc;
+        lacc -= (double)(dd[s].x * wh.x + dd[s].y * wh.y);
+      }
+    }
+    XW[i] = wh;
+  }
+  __syncthreads();
+  // D: rbar_k = gbar - lam L what
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float2 wc = XW[i];
+      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+      if (gj < m - 1) { const float2 wd = XW[i + RW]; d1r = wc.x - wd.x; d1i = wc.y - wd.y; }
+      if (gk < n - 1) { const float2 wr = XW[i + 1]; d2r = wc.x - wr.x; d2i = wc.y - wr.y; }
+      p.rb_out[off + (long long)gj * n + gk] =
+          f4(gb[s].x - lam * d1r, gb[s].y - lam * d1i, gb[s].z - lam * d2r, gb[s].w - lam * d2i);
+    }
+  }
+  double v[1] = {lacc};
+  block_sum<NT, 1>(v, red);
+  if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
+}
+
+// Finalize adjoint: region with a one-pixel halo.
+template <int TV>
+__global__ void __launch_bounds__(ADJ_NT) adj_final_kernel(AdjParams p) {
+  constexpr int RW = ADJ_RW, RH = ADJ_RH, NT = ADJ_NT, R = RW * RH, PPT = R / NT;
+  __shared__ float4 QS[R];
+  __shared__ float2 XW[R];
+  __shared__ double red[NT / 32];
+  const int z = blockIdx.z;
+  const long long off = (long long)z * p.px;
+  const float lam = fmaxf(p.lam_dev[z], 0.f);
+  const int m = p.m, n = p.n;
+  const int gj0 = blockIdx.y * (RH - 2) - 1, gk0 = blockIdx.x * (RW - 2) - 1;
+  const int tid = threadIdx.x;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
+    float4 q = z4;
+    if (p.qK != nullptr && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n)
+      q = __ldg(p.qK + off + (long long)gj * n + gk);
+    QS[i] = q;
+  }
+  __syncthreads();
+  double lacc = 0.0;
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    float2 wh = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const long long o = off + (long long)gj * n + gk;
+      const float4 qc = QS[i];
+      const float4 qu = lj > 0 ? QS[i - RW] : z4;
+      const float4 ql = lk > 0 ? QS[i - 1] : z4;
+      const float dr = qc.x - qu.x + qc.z - ql.z, di = qc.y - qu.y + qc.w - ql.w;
+      const float2 b2 = __ldg(p.b + o);
+      const float2 w = make_float2(b2.x - lam * dr, b2.y - lam * di);
+      wh = proj_C_adj(w, __ldg(p.xbar + o), gj, gk, p.C);
+      if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1) {
+        p.bbar[o] = wh;
+        lacc -= (double)(dr * wh.x + di * wh.y);
+      }
+    }
+    XW[i] = wh;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int i = tid + s * NT;
+    const int lj = i / RW, lk = i % RW;
+    const int gj = gj0 + lj, gk = gk0 + lk;
+    if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      const float2 wc = XW[i];
+      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+      if (gj < m - 1) { const float2 wd = XW[i + RW]; d1r = wc.x - wd.x; d1i = wc.y - wd.y; }
+      if (gk < n - 1) { const float2 wr = XW[i + 1]; d2r = wc.x - wr.x; d2i = wc.y - wr.y; }
+      p.qbK[off + (long long)gj * n + gk] = f4(-lam * d1r, -lam * d1i, -lam * d2r, -lam * d2i);
+    }
+  }
+  double v[1] = {lacc};
+  block_sum<NT, 1>(v, red);
+  if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
+}
+
+__global__ void lambar_finish_kernel(const double* acc, float* out, int batch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < batch) out[i] = (float)acc[i];
+}
+
+// ---------------------------------------------------------------------------
+// Recompute pass that also stores r after every iteration (HIST tiles)
+// ---------------------------------------------------------------------------
+template <int KIND, int TV, int T, int A, int B, int C>
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kernel(PassParams p, float4* hist,
+                                                                                long long hist_plane) {
+  using G = CfgGeom<KIND, A, B, C>;
+  const int z = blockIdx.z;
+  Img I;
+  I.b = p.b + z * p.b_stride;
+  I.ld = p.ld;
+  I.q_in = p.q_in + z * p.d_stride;
+  I.r_in = p.r_in + z * p.d_stride;
+  I.q_out = p.q_out + z * p.d_stride;
+  I.r_out = p.r_out + z * p.d_stride;
+  I.m = p.m;
+  I.n = p.n;
+  const float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
+  I.lam = lam > 0.f ? lam : 0.f;
+  I.alpha = p.alpha;
+  I.C = p.C;
+  I.r_hist = hist + z * p.d_stride;
+  I.hist_plane = hist_plane;
+  run_tile<KIND, TV, T, A, B, C, true>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
+                                       p.nsteps, p.first != 0);
+}
+
+// configurations available to the recompute (a subset of the pass table)
+#define CTV_HIST_CONFIGS(X) \
+  X(2, 0, 4, 64, 32, 256)   \
+  X(7, 1, 4, 2, 8, 8)
+
+template <int KIND, int TV, int T, int A, int B, int C>
+static cudaError_t launch_hist_t(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
+  using G = CfgGeom<KIND, A, B, C>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(fgp_hist_pass_kernel<KIND, TV, T, A, B, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  fgp_hist_pass_kernel<KIND, TV, T, A, B, C><<<grid, G::NT, G::SMEM, s>>>(p, hist, plane);
+  return cudaGetLastError();
+}
+
+template <int TV>
+static cudaError_t launch_hist_tv(int cfg, const PassParams& p, dim3 grid, float4* hist, long long plane,
+                                  cudaStream_t s) {
+  switch (cfg) {
+#define CTV_HIST_CASE(id, kind, T, A, B, C) \
+  case id: return launch_hist_t<kind, TV, T, A, B, C>(p, grid, hist, plane, s);
+    CTV_HIST_CONFIGS(CTV_HIST_CASE)
+#undef CTV_HIST_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_hist(int tv, int cfg, const PassParams& p, dim3 grid, float4* hist, long long plane,
+                               cudaStream_t s) {
+  switch (tv) {
+    case TV1_ISO: return launch_hist_tv<TV1_ISO>(cfg, p, grid, hist, plane, s);
+    case TV1_ANISO: return launch_hist_tv<TV1_ANISO>(cfg, p, grid, hist, plane, s);
+    case TV2_ISO: return launch_hist_tv<TV2_ISO>(cfg, p, grid, hist, plane, s);
+    case TV2_ANISO: return launch_hist_tv<TV2_ANISO>(cfg, p, grid, hist, plane, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static bool hist_config_ok(int cfg) {
+#define CTV_HIST_ID(id, kind, T, A, B, C) if (cfg == id) return true;
+  CTV_HIST_CONFIGS(CTV_HIST_ID)
+#undef CTV_HIST_ID
+  return false;
+}
+
+static cudaError_t launch_adj_step(int tv, const AdjParams& p, int batch, cudaStream_t s) {
+  dim3 grid((p.n + ADJ_RW - 5) / (ADJ_RW - 4), (p.m + ADJ_RH - 5) / (ADJ_RH - 4), batch);
+  switch (tv) {
+    case TV1_ISO: adj_step_kernel<TV1_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    case TV1_ANISO: adj_step_kernel<TV1_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    case TV2_ISO: adj_step_kernel<TV2_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    default: adj_step_kernel<TV2_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_adj_final(int tv, const AdjParams& p, int batch, cudaStream_t s) {
+  dim3 grid((p.n + ADJ_RW - 3) / (ADJ_RW - 2), (p.m + ADJ_RH - 3) / (ADJ_RH - 2), batch);
+  switch (tv) {
+    case TV1_ISO: adj_final_kernel<TV1_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    case TV1_ANISO: adj_final_kernel<TV1_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    case TV2_ISO: adj_final_kernel<TV2_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+    default: adj_final_kernel<TV2_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+static size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct UnrolledLayout {
+  DevStats* st;
+  double* lamacc;
+  std::vector<float4*> ckq, ckr;   // slot s: state after s * ckpt iterations (slot 0 unused: zero state)
+  float4* finq;
+  float4* finr;
+  float4* setq[2];
+  float4* setr[2];
+  float4* hist;                    // ckpt planes
+  float4* rb[3];
+  size_t bytes;
+};
+
+static UnrolledLayout layout(char* base, int batch, int m, int n, int K, int ckpt) {
+  UnrolledLayout L;
+  const size_t plane = al((size_t)batch * m * n * sizeof(float4));
+  const int nseg = (K + ckpt - 1) / ckpt;
+  size_t off = 0;
+  L.st = (DevStats*)(base + off); off += al((size_t)batch * sizeof(DevStats));
+  L.lamacc = (double*)(base + off); off += al((size_t)batch * sizeof(double));
+  L.ckq.assign((size_t)nseg, nullptr);
+  L.ckr.assign((size_t)nseg, nullptr);
+  for (int s = 1; s < nseg; ++s) {
+    L.ckq[(size_t)s] = (float4*)(base + off); off += plane;
+    L.ckr[(size_t)s] = (float4*)(base + off); off += plane;
+  }
+  L.finq = (float4*)(base + off); off += plane;
+  L.finr = (float4*)(base + off); off += plane;
+  for (int i = 0; i < 2; ++i) {
+    L.setq[i] = (float4*)(base + off); off += plane;
+    L.setr[i] = (float4*)(base + off); off += plane;
+  }
+  L.hist = (float4*)(base + off); off += (size_t)ckpt * plane;
+  for (int i = 0; i < 3; ++i) {
+    L.rb[i] = (float4*)(base + off); off += plane;
+  }
+  L.bytes = off;
+  return L;
+}
+
+static int unrolled_config(const ctv_opts* o) {
+  if (o != nullptr && o->config >= 0 && hist_config_ok(o->config)) return o->config;
+  return 2;
+}
+
+struct UnrolledArgs {
+  const void* b;
+  int batch, m, n;
+  const float* lams;
+  const ctv_constraint* C;
+  int tv;
+  const ctv_opts* opts;
+  int ckpt;
+  void* ws;
+  size_t ws_bytes;
+};
+
+static ctv_status check_unrolled(const UnrolledArgs& a, ConsDev* C) {
+  if (a.b == nullptr || a.lams == nullptr || a.ws == nullptr || a.opts == nullptr) return CTV_EINVAL;
+  if (a.batch <= 0 || a.batch > 65535 || a.m <= 0 || a.n <= 0) return CTV_EINVAL;
+  if (a.opts->max_iters < 1 || a.ckpt < 1 || a.opts->warm_start) return CTV_EINVAL;
+  if (!(a.opts->alpha >= 0.f && a.opts->alpha <= 1.f)) return CTV_EINVAL;
+  if (a.tv < 0 || a.tv > 3) return CTV_EINVAL;
+  if (((uintptr_t)a.b & 7) || ((uintptr_t)a.ws & 255)) return CTV_EINVAL;
+  if (!convert_constraint(a.C, a.m, a.n, C)) return CTV_EINVAL;
+  const UnrolledLayout L = layout(nullptr, a.batch, a.m, a.n, a.opts->max_iters, a.ckpt);
+  if (a.ws_bytes < L.bytes) return CTV_EINVAL;
+  return CTV_OK;
+}
+
+static PassParams base_pass(const UnrolledArgs& a, const ConsDev& C) {
+  PassParams p;
+  memset(&p, 0, sizeof(p));
+  p.b = (const float2*)a.b;
+  p.b_stride = (long long)a.m * a.n;
+  p.ld = a.n;
+  p.d_stride = (long long)a.m * a.n;
+  p.m = a.m;
+  p.n = a.n;
+  p.lam_dev = a.lams;
+  p.alpha = a.opts->alpha;
+  p.C = C;
+  p.st = nullptr;
+  return p;
+}
+
+}  // namespace ctv
+
+extern "C" {
+
+size_t ctv_unrolled_workspace_size(int batch, int m, int n, int iters, int ckpt_every) {
+  if (batch <= 0 || m <= 0 || n <= 0 || iters < 1 || ckpt_every < 1) return 0;
+  return ctv::layout(nullptr, batch, m, n, iters, ckpt_every).bytes;
+}
+
+int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const float* lambdas,
+                         const ctv_constraint* C, int tv_type, const ctv_opts* opts, int ckpt_every,
+                         void* workspace, size_t workspace_bytes, ctv_stream stream) {
+  using namespace ctv;
+  UnrolledArgs a{b, batch, m, n, lambdas, C, tv_type, opts, ckpt_every, workspace, workspace_bytes};
+  ConsDev cons;
+  ctv_status st = check_unrolled(a, &cons);
+  if (st != CTV_OK) return st;
+  if (x == nullptr || ((uintptr_t)x & 7)) return CTV_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = opts->max_iters, c = ckpt_every;
+  UnrolledLayout L = layout((char*)workspace, batch, m, n, K, c);
+  const int cfg = unrolled_config(opts);
+  int T = 1;
+  config_info(cfg, &T, nullptr, nullptr, nullptr);
+  std::vector<double> beta;
+  nesterov_betas(K, &beta);
+  PassParams p = base_pass(a, cons);
+  const dim3 grid = pass_grid(cfg, m, n, batch);
+  int k = 1, out = 0;
+  const float4* qin = nullptr;
+  const float4* rin = nullptr;
+  bool first = true;
+  while (k <= K) {
+    const int steps = std::min(std::min(T, K - k + 1), c - ((k - 1) % c));
+    const int kend = k + steps - 1;
+    float4* qo;
+    float4* ro;
+    if (kend == K) { qo = L.finq; ro = L.finr; }
+    else if (kend % c == 0) { qo = L.ckq[(size_t)(kend / c)]; ro = L.ckr[(size_t)(kend / c)]; }
+    else { qo = L.setq[out]; ro = L.setr[out]; out ^= 1; }
+    for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
+    p.nsteps = steps;
+    p.first = first ? 1 : 0;
+    p.q_in = qin;
+    p.r_in = rin;
+    p.q_out = qo;
+    p.r_out = ro;
+    if (launch_pass(tv_type, cfg, p, grid, s) != cudaSuccess) return CTV_ECUDA;
+    count_launch();
+    qin = qo;
+    rin = ro;
+    first = false;
+    k = kend + 1;
+  }
+  if (cudaMemsetAsync(L.st, 0, (size_t)batch * sizeof(DevStats), s) != cudaSuccess) return CTV_ECUDA;
+  GapParams g;
+  memset(&g, 0, sizeof(g));
+  g.b = (const float2*)b;
+  g.b_stride = (long long)m * n;
+  g.ld = n;
+  g.qA = L.finq;
+  g.qB = L.finq;
+  g.d_stride = (long long)m * n;
+  g.default_set = 0;
+  g.x = (float2*)x;
+  g.x_stride = (long long)m * n;
+  g.m = m;
+  g.n = n;
+  g.lam_dev = lambdas;
+  g.alpha = opts->alpha;
+  g.C = cons;
+  g.st = L.st;
+  g.iter = K;
+  g.final_call = 1;
+  if (launch_gap(tv_type, g, batch, s) != cudaSuccess) return CTV_ECUDA;
+  count_launch();
+  return CTV_OK;
+}
+
+int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* lambdabar, int batch, int m, int n,
+                          const float* lambdas, const ctv_constraint* C, int tv_type, const ctv_opts* opts,
+                          int ckpt_every, void* workspace, size_t workspace_bytes, ctv_stream stream) {
+  using namespace ctv;
+  UnrolledArgs a{b, batch, m, n, lambdas, C, tv_type, opts, ckpt_every, workspace, workspace_bytes};
+  ConsDev cons;
+  ctv_status st = check_unrolled(a, &cons);
+  if (st != CTV_OK) return st;
+  if (xbar == nullptr || bbar == nullptr || lambdabar == nullptr) return CTV_EINVAL;
+  if (((uintptr_t)xbar & 7) || ((uintptr_t)bbar & 7) || ((uintptr_t)lambdabar & 3)) return CTV_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = opts->max_iters, c = ckpt_every;
+  UnrolledLayout L = layout((char*)workspace, batch, m, n, K, c);
+  const int cfg = unrolled_config(opts);
+  int T = 1;
+  config_info(cfg, &T, nullptr, nullptr, nullptr);
+  std::vector<double> beta;
+  nesterov_betas(K, &beta);
+  beta.push_back(0.0);   // beta_{K+1} is never used with a nonzero carry
+  const long long px = (long long)m * n;
+  const long long plane = (long long)(al((size_t)batch * px * sizeof(float4)) / sizeof(float4));
+  if (cudaMemsetAsync(L.lamacc, 0, (size_t)batch * sizeof(double), s) != cudaSuccess) return CTV_ECUDA;
+
+  AdjParams ap;
+  memset(&ap, 0, sizeof(ap));
+  ap.b = (const float2*)b;
+  ap.bbar = (float2*)bbar;
+  ap.lamacc = L.lamacc;
+  ap.px = px;
+  ap.m = m;
+  ap.n = n;
+  ap.lam_dev = lambdas;
+  ap.alpha = opts->alpha;
+  ap.C = cons;
+  ap.xbar = (const float2*)xbar;
+  ap.qK = L.finq;
+  ap.qbK = L.rb[0];
+  if (launch_adj_final(tv_type, ap, batch, s) != cudaSuccess) return CTV_ECUDA;
+  count_launch();
+
+  int yi = 0;        // index of the carry buffer (qbar_K first)
+  float yc = 1.f;
+  int nbi = -1;      // index of rbar_{k+1} (-1: zero)
+  PassParams p = base_pass(a, cons);
+  const dim3 grid = pass_grid(cfg, m, n, batch);
+  const int nseg = (K + c - 1) / c;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * c, k1 = std::min(k0 + c, K);
+    // recompute iterations k0+1 .. k1-1, keeping r_{k0+2} .. r_{k1}
+    if (k1 - k0 - 1 > 0) {
+      const float4* qin = sg == 0 ? nullptr : L.ckq[(size_t)sg];
+      const float4* rin = sg == 0 ? nullptr : L.ckr[(size_t)sg];
+      bool first = sg == 0;
+      int kk = k0 + 1, out = 0;
+      while (kk <= k1 - 1) {
+        const int steps = std::min(T, k1 - 1 - kk + 1);
+        for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)kk + i] : 0.f;
+        p.nsteps = steps;
+        p.first = first ? 1 : 0;
+        p.q_in = qin;
+        p.r_in = rin;
+        p.q_out = L.setq[out];
+        p.r_out = L.setr[out];
+        if (launch_hist(tv_type, cfg, p, grid, L.hist + (long long)(kk - k0 - 1) * plane, plane, s) != cudaSuccess)
+          return CTV_ECUDA;
+        count_launch();
+        qin = L.setq[out];
+        rin = L.setr[out];
+        out ^= 1;
+        first = false;
+        kk += steps;
+      }
+    }
+    for (int k = k1; k >= k0 + 1; --k) {
+      const float4* rk;
+      if (k == k0 + 1) rk = sg == 0 ? nullptr : L.ckr[(size_t)sg];
+      else rk = L.hist + (long long)(k - k0 - 2) * plane;
+      int oi = 0;
+      while (oi == yi || oi == nbi) ++oi;
+      ap.r = rk;
+      ap.Y = yi >= 0 ? L.rb[yi] : nullptr;
+      ap.yc = yc;
+      ap.rbn = nbi >= 0 ? L.rb[nbi] : nullptr;
+      ap.rc = (float)(1.0 + beta[(size_t)k]);
+      ap.rb_out = L.rb[oi];
+      if (launch_adj_step(tv_type, ap, batch, s) != cudaSuccess) return CTV_ECUDA;
+      count_launch();
+      // next step k-1: carry = -beta_k rbar_{k+1}, and rbar_k just written
+      yi = nbi;
+      yc = (float)(-beta[(size_t)k]);
+      nbi = oi;
+    }
+  }
+  lambar_finish_kernel<<<(batch + 127) / 128, 128, 0, s>>>(L.lamacc, lambdabar, batch);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
+}
+
+}  // extern "C"

@@ -111,6 +111,8 @@ struct Img {
   int m, n;
   float lam, alpha;
   ConsDev C;
+  float4* r_hist;         // HIST variants: r after inner step it goes to r_hist + it * hist_plane
+  long long hist_plane;
 };
 
 // T iterations of Algorithm 2 on one tile, temporally blocked in shared memory.
@@ -126,7 +128,7 @@ struct Img {
 // Pixels outside the image hold r = x = 0, which is the boundary condition of
 // Eq. (5)/(6). q and b live in registers (each thread owns PPT pixels), r and
 // x in shared memory for the neighbours.
-template <int TV, int T, int RW, int RH, int NT>
+template <int TV, int T, int RW, int RH, int NT, bool HIST = false>
 __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const float* beta,
                                          int nsteps, bool first) {
   constexpr int R = RW * RH;
@@ -198,9 +200,12 @@ __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const flo
         const float4 rc = rs[i];
         const float4 qn = proj_S<TV>(f4(rc.x + c8 * d1r, rc.y + c8 * d1i, rc.z + c8 * d2r, rc.w + c8 * d2i), I.alpha);
         const float4 qo = qreg[s];
-        rs[i] = f4(qn.x + bt * (qn.x - qo.x), qn.y + bt * (qn.y - qo.y),
-                   qn.z + bt * (qn.z - qo.z), qn.w + bt * (qn.w - qo.w));
+        const float4 rn = f4(qn.x + bt * (qn.x - qo.x), qn.y + bt * (qn.y - qo.y),
+                             qn.z + bt * (qn.z - qo.z), qn.w + bt * (qn.w - qo.w));
+        rs[i] = rn;
         qreg[s] = qn;
+        if (HIST && lj >= T && lj < RH - T && lk >= T && lk < RW - T)
+          I.r_hist[it * I.hist_plane + (long long)gj * I.n + gk] = rn;
       }
     }
     __syncthreads();
@@ -216,6 +221,123 @@ __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const flo
       const long long o = (long long)gj * I.n + gk;
       I.q_out[o] = qreg[s];
       I.r_out[o] = rs[i];
+    }
+  }
+}
+
+// T iterations of Algorithm 2 on one tile, with column-strip ownership.
+//
+// Same contract as fgp_tile (an RW x RH region with a T-pixel halo, only the
+// interior written back), but each thread owns PPT vertically consecutive pixels
+// of one column: a warp covers 32 adjacent columns, WX warps side by side and WY
+// warps stacked give RW = 32 WX and RH = PPT WY. q, r and the transient x of the
+// owned pixels stay in registers, so the vertical neighbours of the stencil
+// (r above for L^T, x below for L) come from registers except at the ends of
+// a strip. Shared memory holds only what other threads need: p2 = (r2, s2) of
+// every pixel (left neighbour of L^T), x of every pixel (right and, at strip
+// ends, lower neighbour of L) and p1 = (r1, s1) of each strip's last row (upper
+// neighbour of the next strip). b is re-read through the read-only cache.
+template <int TV, int T, int WX, int WY, int PPT, bool HIST = false>
+__device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, const float* beta, int nsteps,
+                                               bool first) {
+  constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH;
+  extern __shared__ float4 smem4[];
+  float2* P2 = reinterpret_cast<float2*>(smem4);      // R
+  float2* X = P2 + R;                                  // R
+  float2* P1B = X + R;                                 // WY * RW
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int wx = warp % WX, wy = warp / WX;
+  const int lk = wx * 32 + lane;
+  const int lj0 = wy * PPT;
+  const int gk = k0 - T + lk;
+  const int gj0 = j0 - T + lj0;
+  const bool colin = (unsigned)gk < (unsigned)I.n;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const float2 z2 = make_float2(0.f, 0.f);
+
+  float4 q[PPT], r[PPT];
+  float2 x[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int gj = gj0 + s;
+    q[s] = z4;
+    r[s] = z4;
+    if (!first && colin && (unsigned)gj < (unsigned)I.m) {
+      const long long o = (long long)gj * I.n + gk;
+      q[s] = __ldg(I.q_in + o);
+      r[s] = __ldg(I.r_in + o);
+    }
+    P2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
+  }
+  P1B[wy * RW + lk] = make_float2(r[PPT - 1].x, r[PPT - 1].y);
+  __syncthreads();
+
+  const float lam = I.lam;
+  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
+  const bool has_right = lk < RW - 1 && gk < I.n - 1;
+  for (int it = 0; it < nsteps; ++it) {
+    // phase 1: x = P_C(b - lam L^T r)
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int gj = gj0 + s;
+      x[s] = z2;
+      if (colin && (unsigned)gj < (unsigned)I.m) {
+        float2 up;
+        if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
+        else up = wy > 0 ? P1B[(wy - 1) * RW + lk] : z2;
+        const float2 left = lk > 0 ? P2[(lj0 + s) * RW + lk - 1] : z2;
+        // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]
+        const float dre = r[s].x - up.x + r[s].z - left.x;
+        const float dim = r[s].y - up.y + r[s].w - left.y;
+        const float2 bb = __ldg(I.b + (long long)gj * I.ld + gk);
+        x[s] = proj_C(make_float2(bb.x - lam * dre, bb.y - lam * dim), gj, gk, I.C);
+      }
+      X[(lj0 + s) * RW + lk] = x[s];
+    }
+    __syncthreads();
+    // phase 2: q = P_S(r + L x / (8 lam)), r' = q + beta (q - q_prev)
+    const float bt = beta[it];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int gj = gj0 + s;
+      if (colin && (unsigned)gj < (unsigned)I.m) {
+        float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+        if (gj < I.m - 1) {
+          float2 xd;
+          if (s < PPT - 1) xd = x[s + 1];
+          else xd = (lj0 + s + 1 < RH) ? X[(lj0 + s + 1) * RW + lk] : x[s];
+          d1r = x[s].x - xd.x;
+          d1i = x[s].y - xd.y;
+        }
+        if (has_right) {
+          const float2 xr = X[(lj0 + s) * RW + lk + 1];
+          d2r = x[s].x - xr.x;
+          d2i = x[s].y - xr.y;
+        }
+        const float4 qn = proj_S<TV>(f4(r[s].x + c8 * d1r, r[s].y + c8 * d1i, r[s].z + c8 * d2r, r[s].w + c8 * d2i),
+                                     I.alpha);
+        r[s] = f4(qn.x + bt * (qn.x - q[s].x), qn.y + bt * (qn.y - q[s].y),
+                  qn.z + bt * (qn.z - q[s].z), qn.w + bt * (qn.w - q[s].w));
+        q[s] = qn;
+        if (HIST && lk >= T && lk < RW - T && lj0 + s >= T && lj0 + s < RH - T)
+          I.r_hist[it * I.hist_plane + (long long)gj * I.n + gk] = r[s];
+      }
+      P2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
+    }
+    P1B[wy * RW + lk] = make_float2(r[PPT - 1].x, r[PPT - 1].y);
+    __syncthreads();
+  }
+
+  if (lk >= T && lk < RW - T && colin) {
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int lj = lj0 + s, gj = gj0 + s;
+      if (lj >= T && lj < RH - T && (unsigned)gj < (unsigned)I.m) {
+        const long long o = (long long)gj * I.n + gk;
+        I.q_out[o] = q[s];
+        I.r_out[o] = r[s];
+      }
     }
   }
 }

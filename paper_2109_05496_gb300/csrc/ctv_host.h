@@ -34,7 +34,9 @@ ctv_status run_denoise(const DenoiseCall& c);
 size_t denoise_workspace_bytes(int batch, int m, int n);
 bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out);
 void nesterov_betas(int K, std::vector<double>* beta);
-int default_config(int m, int n, int iters);
+int default_config(int m, int n, int iters, int tv);
+int tuned_config(int m, int n, int tv);   // -1 when the size class / TV type is not tuned
+int size_class(int m, int n);
 int num_configs();
 bool config_info(int i, int* T, int* RW, int* RH, int* NT);
 

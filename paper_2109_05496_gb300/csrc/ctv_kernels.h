@@ -1,0 +1,61 @@
+// Kernel parameter blocks and launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ctv_device.cuh"
+
+namespace ctv {
+
+// One launch of the fused FGP pass over an equally sized batch (blockIdx.z = image).
+struct PassParams {
+  const float2* b;
+  long long b_stride;
+  int ld;
+  const float4* q_in;
+  const float4* r_in;
+  float4* q_out;
+  float4* r_out;
+  long long d_stride;
+  int m, n;
+  float lam;
+  const float* lam_dev;
+  float alpha;
+  ConsDev C;
+  const DevStats* st;
+  float beta[8];
+  int nsteps;
+  int first;
+};
+
+// One launch of the finalize / gap evaluation over an equally sized batch.
+struct GapParams {
+  const float2* b;
+  long long b_stride;
+  int ld;
+  const float4* qA;
+  const float4* qB;
+  long long d_stride;
+  int default_set;   // 0: qA, 1: qB, 2: dual_in
+  const float4* dual_in;
+  int zero_q;        // q = 0 (no iteration has run)
+  float2* x;         // nullable
+  long long x_stride;
+  float4* q_export;  // nullable, stride d_stride
+  int m, n;
+  float lam;
+  const float* lam_dev;
+  float alpha;
+  ConsDev C;
+  DevStats* st;
+  int iter;
+  double gap_tol;
+  int final_call;
+};
+
+cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s);
+cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s);
+// Grid of the fused pass for configuration cfg over an m x n image batch.
+dim3 pass_grid(int cfg, int m, int n, int batch);
+
+}  // namespace ctv

@@ -16,33 +16,16 @@
 #include <vector>
 
 #include "ctv.h"
+#include "ctv_configs.cuh"
 #include "ctv_device.cuh"
 #include "ctv_host.h"
+#include "ctv_kernels.h"
 
 namespace ctv {
 
-struct PassParams {
-  const float2* b;
-  long long b_stride;
-  int ld;
-  const float4* q_in;
-  const float4* r_in;
-  float4* q_out;
-  float4* r_out;
-  long long d_stride;
-  int m, n;
-  float lam;
-  const float* lam_dev;
-  float alpha;
-  ConsDev C;
-  const DevStats* st;
-  float beta[8];
-  int nsteps;
-  int first;
-};
-
-template <int TV, int T, int RW, int RH, int NT>
-__global__ void __launch_bounds__(NT) fgp_pass_kernel(PassParams p) {
+template <int KIND, int TV, int T, int A, int B, int C>
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(PassParams p) {
+  using G = CfgGeom<KIND, A, B, C>;
   const int z = blockIdx.z;
   if (p.st != nullptr && *(volatile const int*)&p.st[z].stop) return;
   Img I;
@@ -58,33 +41,9 @@ __global__ void __launch_bounds__(NT) fgp_pass_kernel(PassParams p) {
   I.lam = lam > 0.f ? lam : 0.f;
   I.alpha = p.alpha;
   I.C = p.C;
-  fgp_tile<TV, T, RW, RH, NT>(I, blockIdx.y * (RH - 2 * T), blockIdx.x * (RW - 2 * T), p.beta,
-                              p.nsteps, p.first != 0);
+  run_tile<KIND, TV, T, A, B, C>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta, p.nsteps,
+                                 p.first != 0);
 }
-
-struct GapParams {
-  const float2* b;
-  long long b_stride;
-  int ld;
-  const float4* qA;
-  const float4* qB;
-  long long d_stride;
-  int default_set;   // 0: qA, 1: qB, 2: dual_in
-  const float4* dual_in;
-  int zero_q;        // q = 0 (no iteration has run)
-  float2* x;         // nullable
-  long long x_stride;
-  float4* q_export;  // nullable, stride d_stride
-  int m, n;
-  float lam;
-  const float* lam_dev;
-  float alpha;
-  ConsDev C;
-  DevStats* st;
-  int iter;
-  double gap_tol;
-  int final_call;
-};
 
 // Grid front end of gap_tile: blockIdx.z is the image of an equally sized batch.
 template <int TV>
@@ -119,47 +78,43 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
 }
 
 // ----------------------------------------------------------------------------
-// Configurations of the fused pass
+// Configurations of the fused pass (table in ctv_configs.cuh)
 // ----------------------------------------------------------------------------
 struct Cfg {
   int T, RW, RH, NT;
 };
-static const Cfg kCfgs[] = {
-    {1, 64, 16, 256},
-    {2, 64, 32, 256},
-    {4, 64, 32, 256},
-    {4, 64, 64, 512},
-    {8, 64, 64, 512},
-};
+#define CTV_CFG_ROW(id, kind, T, A, B, C) \
+  {T, CfgGeom<kind, A, B, C>::RW, CfgGeom<kind, A, B, C>::RH, CfgGeom<kind, A, B, C>::NT},
+static const Cfg kCfgs[] = {CTV_PASS_CONFIGS(CTV_CFG_ROW)};
+#undef CTV_CFG_ROW
 static const int kNumCfgs = (int)(sizeof(kCfgs) / sizeof(kCfgs[0]));
 
-template <int TV, int T, int RW, int RH, int NT>
+template <int KIND, int TV, int T, int A, int B, int C>
 static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
-  constexpr size_t smem = (size_t)RW * RH * (sizeof(float4) + sizeof(float2));
+  using G = CfgGeom<KIND, A, B, C>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<TV, T, RW, RH, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<KIND, TV, T, A, B, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  fgp_pass_kernel<TV, T, RW, RH, NT><<<grid, NT, smem, s>>>(p);
+  fgp_pass_kernel<KIND, TV, T, A, B, C><<<grid, G::NT, G::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int TV>
 static cudaError_t launch_pass_tv(int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_pass_t<TV, 1, 64, 16, 256>(p, grid, s);
-    case 1: return launch_pass_t<TV, 2, 64, 32, 256>(p, grid, s);
-    case 2: return launch_pass_t<TV, 4, 64, 32, 256>(p, grid, s);
-    case 3: return launch_pass_t<TV, 4, 64, 64, 512>(p, grid, s);
-    case 4: return launch_pass_t<TV, 8, 64, 64, 512>(p, grid, s);
+#define CTV_CFG_CASE(id, kind, T, A, B, C) \
+  case id: return launch_pass_t<kind, TV, T, A, B, C>(p, grid, s);
+    CTV_PASS_CONFIGS(CTV_CFG_CASE)
+#undef CTV_CFG_CASE
   }
   return cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
+cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
   switch (tv) {
     case TV1_ISO: return launch_pass_tv<TV1_ISO>(cfg, p, grid, s);
     case TV1_ANISO: return launch_pass_tv<TV1_ANISO>(cfg, p, grid, s);
@@ -169,7 +124,7 @@ static cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, 
   return cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
+cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
   dim3 grid((p.n + GAP_RW - 3) / (GAP_RW - 2), (p.m + GAP_RH - 3) / (GAP_RH - 2), batch);
   switch (tv) {
     case TV1_ISO: fgp_gap_kernel<TV1_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
@@ -181,10 +136,18 @@ static cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_
   return cudaGetLastError();
 }
 
-int default_config(int m, int n, int iters) {
-  (void)m;
-  (void)n;
+dim3 pass_grid(int cfg, int m, int n, int batch) {
+  const Cfg& cf = kCfgs[cfg];
+  return dim3((n + (cf.RW - 2 * cf.T) - 1) / (cf.RW - 2 * cf.T), (m + (cf.RH - 2 * cf.T) - 1) / (cf.RH - 2 * cf.T),
+              batch);
+}
+
+int default_config(int m, int n, int iters, int tv) {
   if (iters < 2) return 0;
+  if (m > 0 && n > 0) {
+    const int t = tuned_config(m, n, tv);
+    if (t >= 0) return t;
+  }
   return 2;
 }
 
@@ -251,7 +214,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
   if (K < 0 || check_every < 0 || !(gap_tol >= 0.0) || !(alpha >= 0.f && alpha <= 1.f)) return CTV_EINVAL;
   if (warm && c.dual_state == nullptr) return CTV_EINVAL;
   if (cfg >= kNumCfgs || cfg < -1) return CTV_EINVAL;
-  if (cfg < 0) cfg = default_config(c.m, c.n, K);
+  if (cfg < 0) cfg = default_config(c.m, c.n, K, c.tv);
   ConsDev C;
   if (!convert_constraint(c.C, c.m, c.n, &C)) return CTV_EINVAL;
   if (c.workspace_bytes < denoise_workspace_bytes(c.batch, c.m, c.n)) return CTV_EINVAL;
@@ -308,8 +271,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
     p.alpha = alpha;
     p.C = C;
     p.st = st;
-    dim3 grid((c.n + (cf.RW - 2 * cf.T) - 1) / (cf.RW - 2 * cf.T),
-              (c.m + (cf.RH - 2 * cf.T) - 1) / (cf.RH - 2 * cf.T), c.batch);
+    const dim3 grid = pass_grid(cfg, c.m, c.n, c.batch);
     if (grid.y > 65535) return CTV_EINVAL;
     int k = 1;
     int out = 0;

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ctv.h"
+#include "ctv_configs.cuh"
 #include "ctv_device.cuh"
 #include "ctv_host.h"
 
@@ -53,8 +54,9 @@ struct ListPassParams {
   float beta[8];
 };
 
-template <int T, int RW, int RH, int NT>
-__global__ void __launch_bounds__(NT) fgp_pass_list_kernel(ListPassParams p) {
+template <int KIND, int T, int A, int B, int C>
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kernel(ListPassParams p) {
+  using G = CfgGeom<KIND, A, B, C>;
   const WorkItem w = p.items[blockIdx.x];
   const PlanImg d = p.imgs[w.img];
   if (*(volatile const int*)&d.st->stop) return;
@@ -70,13 +72,13 @@ __global__ void __launch_bounds__(NT) fgp_pass_list_kernel(ListPassParams p) {
   I.lam = d.lam;
   I.alpha = d.alpha;
   I.C = d.C;
-  const int j0 = (w.tile / d.tiles_x) * (RH - 2 * T), k0 = (w.tile % d.tiles_x) * (RW - 2 * T);
+  const int j0 = (w.tile / d.tiles_x) * (G::RH - 2 * T), k0 = (w.tile % d.tiles_x) * (G::RW - 2 * T);
   const bool first = p.first != 0;
   switch (d.tv) {
-    case TV1_ISO: fgp_tile<TV1_ISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
-    case TV1_ANISO: fgp_tile<TV1_ANISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
-    case TV2_ISO: fgp_tile<TV2_ISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
-    default: fgp_tile<TV2_ANISO, T, RW, RH, NT>(I, j0, k0, p.beta, p.nsteps, first); break;
+    case TV1_ISO: run_tile<KIND, TV1_ISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
+    case TV1_ANISO: run_tile<KIND, TV1_ANISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
+    case TV2_ISO: run_tile<KIND, TV2_ISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
+    default: run_tile<KIND, TV2_ANISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
   }
 }
 
@@ -122,26 +124,23 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
   gap_commit(d.st, acc, d.gnblk, d.lam, false, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
 }
 
-template <int T, int RW, int RH, int NT>
+template <int KIND, int T, int A, int B, int C>
 static cudaError_t launch_list_t(const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
-  constexpr size_t smem = (size_t)RW * RH * (sizeof(float4) + sizeof(float2));
+  using G = CfgGeom<KIND, A, B, C>;
   if (set_attr) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_pass_list_kernel<T, RW, RH, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaSuccess;
+    return cudaFuncSetAttribute(fgp_pass_list_kernel<KIND, T, A, B, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)G::SMEM);
   }
-  fgp_pass_list_kernel<T, RW, RH, NT><<<nblocks, NT, smem, s>>>(p);
+  fgp_pass_list_kernel<KIND, T, A, B, C><<<nblocks, G::NT, G::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_list(int cfg, const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
   switch (cfg) {
-    case 0: return launch_list_t<1, 64, 16, 256>(p, nblocks, s, set_attr);
-    case 1: return launch_list_t<2, 64, 32, 256>(p, nblocks, s, set_attr);
-    case 2: return launch_list_t<4, 64, 32, 256>(p, nblocks, s, set_attr);
-    case 3: return launch_list_t<4, 64, 64, 512>(p, nblocks, s, set_attr);
-    case 4: return launch_list_t<8, 64, 64, 512>(p, nblocks, s, set_attr);
+#define CTV_CFG_CASE(id, kind, T, A, B, C) \
+  case id: return launch_list_t<kind, T, A, B, C>(p, nblocks, s, set_attr);
+    CTV_PASS_CONFIGS(CTV_CFG_CASE)
+#undef CTV_CFG_CASE
   }
   return cudaErrorInvalidValue;
 }
@@ -240,7 +239,7 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   if (opts->max_iters < 0 || opts->check_every < 0 || !(opts->gap_tol >= 0.0) || opts->warm_start) return CTV_EINVAL;
   int cfg = opts->config;
   if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
-  if (cfg < 0) cfg = default_config(0, 0, opts->max_iters);
+  if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1);
   int T = 1, RW = 0, RH = 0, NT = 0;
   config_info(cfg, &T, &RW, &RH, &NT);
   const int TW = RW - 2 * T, TH = RH - 2 * T;

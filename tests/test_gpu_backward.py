@@ -1,0 +1,147 @@
+"""GPU differentiation through unrolled FGP (ctv_unrolled_forward / _backward,
+UnrolledFGP) against the oracle's FP64 autograd of Algorithm 2, against FP64
+finite differences of the oracle, and (forward) bit-for-bit against
+ctv_denoise_batched with the same configuration."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2109_05496_gb300 as ctv
+from oracle.fgp import fgp
+from oracle.ops import DT
+from phantoms import noisy_phantom, to_c64
+from tests.helpers import TV_NAMES, f32, oracle_constraint
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_grads(b_np, lams, K, tv, alpha, Co, xbar_np):
+    """d<xbar, x>/db and d<xbar, x>/dlam of the oracle in FP64, per image."""
+    gb, gl = [], []
+    for i in range(b_np.shape[0]):
+        bb = torch.tensor(b_np[i].astype(np.complex128))
+        bu = bb.real.clone().requires_grad_(True)
+        bv = bb.imag.clone().requires_grad_(True)
+        lam = torch.tensor(f32(lams[i]), dtype=DT, requires_grad=True)
+        res = fgp((bu, bv), lam, K, tv, f32(alpha), Co)
+        xb = torch.tensor(xbar_np[i].astype(np.complex128))
+        loss = (res.x[0] * xb.real).sum() + (res.x[1] * xb.imag).sum()
+        du, dv, dl = torch.autograd.grad(loss, (bu, bv, lam))
+        gb.append((du + 1j * dv).numpy())
+        gl.append(float(dl))
+    return np.stack(gb), np.array(gl)
+
+
+def gpu_grads(b_np, lams, K, tv, alpha, C, xbar_np, ckpt, config=-1):
+    b = torch.from_numpy(b_np.astype(np.complex64)).cuda().requires_grad_(True)
+    lt = torch.tensor(lams, dtype=torch.float32, device="cuda", requires_grad=True)
+    x = ctv.denoise_unrolled(b, lt, tv, K, C, alpha, ckpt, config)
+    xb = torch.from_numpy(xbar_np.astype(np.complex64)).cuda()
+    # <xbar, x> in the real-pair inner product; torch's complex gradient is dL/dRe + i dL/dIm
+    loss = (x.real * xb.real).sum() + (x.imag * xb.imag).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return x.detach(), b.grad.cpu().numpy(), lt.grad.cpu().numpy()
+
+
+def make(Bn, m, n, seed, sigma=0.15):
+    imgs = np.stack([to_c64(noisy_phantom(m, n, sigma, seed=seed + i)[1]) for i in range(Bn)])
+    rng = np.random.default_rng(seed + 99)
+    xbar = (rng.standard_normal((Bn, m, n)) + 1j * rng.standard_normal((Bn, m, n))).astype(np.complex64)
+    return imgs, xbar
+
+
+@pytest.mark.parametrize("tv", TV_NAMES)
+@pytest.mark.parametrize("kind", ["amp", "amp_rect", "none"])
+def test_unrolled_gradient_matches_oracle(tv, kind):
+    Bn, m, n, K, ckpt = 2, 37, 70, 13, 4
+    imgs, xbar = make(Bn, m, n, seed=7)
+    lams = [0.04, 0.09]
+    if kind == "none":
+        C, Co = ctv.NO_CONSTRAINT, None
+    elif kind == "amp":
+        C, Co = ctv.Constraint(amp_max=1.0), oracle_constraint(1.0)
+    else:
+        r = (3, 5, 30, 61)
+        C, Co = ctv.Constraint(amp_max=1.0, rect=r), oracle_constraint(1.0, rect=r)
+    _, gb, gl = gpu_grads(imgs, lams, K, tv, 0.5, C, xbar, ckpt)
+    ob, ol = oracle_grads(imgs, lams, K, tv, 0.5, Co, xbar)
+    scale = np.abs(ob).max()
+    assert np.abs(gb - ob).max() <= 2e-3 * scale, np.abs(gb - ob).max() / scale
+    np.testing.assert_allclose(gl, ol, rtol=2e-3, atol=2e-3 * np.abs(ol).max())
+
+
+@pytest.mark.parametrize("ckpt", [1, 3, 10, 50])
+def test_checkpoint_spacing_does_not_change_result(ckpt):
+    imgs, xbar = make(1, 40, 33, seed=3)
+    ref = None
+    _, gb, gl = gpu_grads(imgs, [0.05], 10, "tv1_iso", 0.5, ctv.Constraint(amp_max=1.0), xbar, ckpt)
+    _, gb1, gl1 = gpu_grads(imgs, [0.05], 10, "tv1_iso", 0.5, ctv.Constraint(amp_max=1.0), xbar, 10)
+    assert np.array_equal(gb, gb1) and np.array_equal(gl, gl1)
+
+
+def test_unrolled_forward_equals_batched_denoise():
+    imgs, _ = make(3, 64, 96, seed=11)
+    b = torch.from_numpy(imgs).cuda()
+    lams = torch.tensor([0.02, 0.05, 0.08], device="cuda")
+    for tv in TV_NAMES:
+        x1 = ctv.denoise_unrolled(b, lams, tv, 25, ctv.Constraint(amp_max=1.0), 0.5, 10, 2)
+        x2 = ctv.denoise(b, lams, tv, 25, ctv.Constraint(amp_max=1.0), 0.5, config=2)
+        assert torch.equal(x1, x2)
+
+
+def test_finite_differences_fp64_32x32():
+    # FP64 central differences of the oracle's loss ||x - x_gt||^2 along random
+    # directions against the GPU gradient (the gradient of the same loss)
+    m = n = 32
+    K = 20
+    clean, noisy = noisy_phantom(m, n, 0.15, seed=5)
+    b_np = to_c64(noisy)[None]
+    gt = torch.tensor(clean)
+    lam = 0.06
+    Co = oracle_constraint(1.0)
+
+    def loss64(bc, lamv):
+        res = fgp((bc.real.clone(), bc.imag.clone()), lamv, K, "tv1_iso", 0.5, Co)
+        return float(((res.x[0] - gt.real) ** 2).sum() + ((res.x[1] - gt.imag) ** 2).sum())
+
+    b = torch.from_numpy(b_np).cuda().requires_grad_(True)
+    lt = torch.tensor([lam], dtype=torch.float32, device="cuda", requires_grad=True)
+    x = ctv.denoise_unrolled(b, lt, "tv1_iso", K, ctv.Constraint(amp_max=1.0), 0.5, 5)
+    g = torch.from_numpy(clean.astype(np.complex64)).cuda()[None]
+    loss = ((x - g).abs() ** 2).sum()
+    loss.backward()
+    gb = b.grad.cpu().numpy()[0].astype(np.complex128)
+    bc = torch.tensor(b_np[0].astype(np.complex128))
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    for _ in range(3):
+        d = torch.tensor(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))
+        fd = (loss64(bc + h * d, f32(lam)) - loss64(bc - h * d, f32(lam))) / (2 * h)
+        an = float((gb.real * d.real.numpy()).sum() + (gb.imag * d.imag.numpy()).sum())
+        assert abs(fd - an) <= 2e-3 * max(1.0, abs(fd))
+    fd = (loss64(bc, f32(lam) + h) - loss64(bc, f32(lam) - h)) / (2 * h)
+    assert abs(fd - float(lt.grad)) <= 2e-3 * max(1.0, abs(fd))
+
+
+def test_full_size_gradient_window():
+    # the differentiation workload: 8 x 1024^2, 50 iterations, checkpoints every 10;
+    # the gradient at sample pixels against the oracle on a window around them
+    # (the gradient at a pixel depends only on inputs within about 3K pixels)
+    Bn, m, n, K = 8, 1024, 1024, 50
+    imgs = np.stack([to_c64(noisy_phantom(m, n, 0.1, seed=500 + i)[1]) for i in range(Bn)])
+    rng = np.random.default_rng(8)
+    xbar = (rng.standard_normal((Bn, m, n)) + 1j * rng.standard_normal((Bn, m, n))).astype(np.complex64)
+    lams = np.linspace(0.02, 0.09, Bn)
+    C = ctv.Constraint(amp_max=1.0)
+    _, gb, gl = gpu_grads(imgs, lams, K, "tv1_iso", 0.5, C, xbar, 10)
+    assert np.all(np.isfinite(gb)) and np.all(np.isfinite(gl))
+    R = 3 * K + 8
+    for (i, j, k) in [(0, 500, 500), (5, 3, 1020)]:
+        j0, j1 = max(0, j - R), min(m, j + R + 1)
+        k0, k1 = max(0, k - R), min(n, k + R + 1)
+        ob, _ = oracle_grads(imgs[i:i + 1, j0:j1, k0:k1], [lams[i]], K, "tv1_iso", 0.5, oracle_constraint(1.0),
+                             xbar[i:i + 1, j0:j1, k0:k1])
+        want = ob[0, j - j0, k - k0]
+        scale = np.abs(ob).max()
+        assert abs(gb[i, j, k] - want) <= 2e-3 * scale

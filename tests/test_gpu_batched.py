@@ -33,7 +33,7 @@ def plan_images(imgs, lams, types, rects=None):
     return out
 
 
-@pytest.mark.parametrize("config", [0, 2, 4])
+@pytest.mark.parametrize("config", [row[0] for row in __import__("paper_2109_05496_gb300.build", fromlist=["x"]).config_table()])
 def test_plan_matches_oracle_and_loop(config):
     shapes, lams, types, imgs = make_batch(14, 3, 150, seed=5)
     ims = plan_images(imgs, lams, types)

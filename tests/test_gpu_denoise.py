@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import paper_2109_05496_gb300 as ctv
+from paper_2109_05496_gb300 import build as ctv_build
 from oracle.fgp import dual_value, primal_value
 from oracle.ops import in_S, P_C as oracle_PC
 from phantoms import noisy_phantom, phantom, support_rect, to_c64
@@ -20,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 XTOL = 1e-4
 OBJTOL = 1e-6
+CONFIGS = [row[0] for row in ctv_build.config_table()]
 
 
 def cons_pair(kind, m, n, seed=0):
@@ -58,7 +60,7 @@ def check_parity(x_gpu, res, b_pair, b_np, lam, tv, alpha):
 
 
 # --------------------------------------------------------------- C1: 256^2, 100 iterations
-@pytest.mark.parametrize("config", list(range(5)))
+@pytest.mark.parametrize("config", CONFIGS)
 def test_phantom_256_tv1_iso(config):
     _, noisy = noisy_phantom(256, 256, 0.1, seed=1)
     Cg, Co = cons_pair("amp", 256, 256)
@@ -75,7 +77,7 @@ def test_phantom_256_tv1_iso(config):
 
 
 # --------------------------------------------------------------- all TV types x constraints, ragged tiles
-@pytest.mark.parametrize("config", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("config", CONFIGS)
 @pytest.mark.parametrize("kind", ["none", "amp", "amp_rect", "amp_mask"])
 @pytest.mark.parametrize("tv", TV_NAMES)
 def test_types_constraints_ragged(tv, kind, config):
@@ -91,7 +93,7 @@ def test_types_constraints_ragged(tv, kind, config):
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 37), (45, 1), (2, 3), (3, 2), (17, 65), (129, 63), (200, 7)])
 @pytest.mark.parametrize("tv", TV_NAMES)
-@pytest.mark.parametrize("config", [0, 4])
+@pytest.mark.parametrize("config", CONFIGS)
 def test_degenerate_shapes(shape, tv, config):
     m, n = shape
     rng = np.random.default_rng(m * 1000 + n)
