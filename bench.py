@@ -56,7 +56,8 @@ def read_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_2109_05496_gb300/csrc/ctv_device.cuh", "paper_2109_05496_gb300/csrc/denoise.cu"):
+    for rel in ("paper_2109_05496_gb300/csrc/ctv_device.cuh", "paper_2109_05496_gb300/csrc/pass_tv.cuh",
+                "paper_2109_05496_gb300/csrc/ctv_configs.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -321,9 +322,7 @@ def main():
 
 
 def default_config_id(lib) -> int:
-    # the library picks config 2 (4 iterations per pass) for K >= 2; mirrored here for the report
-    import ctypes
-    return 2 if ITERS >= 2 else 0
+    return int(lib.ctv_default_config(M, N, ITERS, 0))
 
 
 # ----------------------------------------------------------------------------- other workloads

@@ -51,6 +51,7 @@ SIGNATURES = {
     "ctv_status_string": (C.c_char_p, [c_int]),
     "ctv_abi_version": (c_int, []),
     "ctv_num_configs": (c_int, []),
+    "ctv_default_config": (c_int, [c_int, c_int, c_int, c_int]),
     "ctv_config_info": (c_int, [c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
     "ctv_denoise_workspace_size": (c_size_t, [c_int, c_int, c_int]),
     "ctv_size_class": (c_int, [c_int, c_int]),

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
 // configurations available to the recompute (a subset of the pass table)
 #define CTV_HIST_CONFIGS(X) \
   X(2, 0, 4, 64, 32, 256)   \
-  X(7, 1, 4, 2, 8, 8)
+  X(5, 1, 6, 2, 8, 8)
 
 template <int KIND, int TV, int T, int A, int B, int C>
 static cudaError_t launch_hist_t(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {

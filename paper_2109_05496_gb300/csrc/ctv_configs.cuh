@@ -13,15 +13,14 @@
   X(0, 0, 1, 64, 16, 256)    \
   X(1, 0, 2, 64, 32, 256)    \
   X(2, 0, 4, 64, 32, 256)    \
-  X(3, 0, 4, 64, 64, 512)    \
-  X(4, 0, 8, 64, 64, 512)    \
-  X(5, 1, 2, 2, 4, 8)        \
-  X(6, 1, 4, 2, 4, 8)        \
-  X(7, 1, 4, 2, 8, 8)        \
-  X(8, 1, 6, 2, 8, 8)        \
-  X(9, 1, 4, 4, 4, 8)        \
-  X(10, 1, 3, 2, 8, 4)       \
-  X(11, 1, 8, 2, 8, 8)
+  X(3, 1, 4, 2, 4, 8)        \
+  X(4, 1, 4, 2, 8, 8)        \
+  X(5, 1, 6, 2, 8, 8)        \
+  X(6, 1, 8, 2, 8, 8)        \
+  X(7, 1, 3, 2, 8, 4)        \
+  X(8, 1, 6, 4, 4, 8)        \
+  X(9, 1, 4, 1, 4, 8)        \
+  X(10, 1, 2, 1, 4, 8)
 
 namespace ctv {
 
@@ -31,15 +30,15 @@ struct CfgGeom {
   static constexpr int RH = KIND == 0 ? B : B * C;
   static constexpr int NT = KIND == 0 ? C : 32 * A * B;
   static constexpr size_t SMEM = KIND == 0 ? (size_t)RW * RH * (sizeof(float4) + sizeof(float2))
-                                           : (size_t)RW * RH * 2 * sizeof(float2) + (size_t)B * RW * sizeof(float2);
+                                           : (size_t)RW * RH * 3 * sizeof(float2) + (size_t)B * RW * sizeof(float2);
 };
 
-template <int KIND, int TV, int T, int A, int B, int C, bool HIST = false>
+template <int KIND, int TV, int T, int A, int B, int C, bool HIST = false, int CONS = CONS_GEN>
 __device__ __forceinline__ void run_tile(const Img& I, int j0, int k0, const float* beta, int nsteps, bool first) {
   if constexpr (KIND == 0) {
     fgp_tile<TV, T, A, B, C, HIST>(I, j0, k0, beta, nsteps, first);
   } else {
-    fgp_strip_tile<TV, T, A, B, C, HIST>(I, j0, k0, beta, nsteps, first);
+    fgp_strip_tile<TV, T, A, B, C, HIST, CONS>(I, j0, k0, beta, nsteps, first);
   }
 }
 

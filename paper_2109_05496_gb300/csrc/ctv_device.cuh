@@ -225,6 +225,32 @@ __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const flo
   }
 }
 
+// Constraint specialisations of P_C for the column-strip kernel.
+enum { CONS_NONE = 0, CONS_AMP = 1, CONS_RECT = 2, CONS_GEN = 3 };
+
+__device__ __forceinline__ float2 proj_amp(float2 w, float amax) {
+  const float a2 = w.x * w.x + w.y * w.y;
+  if (a2 > amax * amax) {
+    const float s = amax * rsqrtf(a2);
+    w.x *= s;
+    w.y *= s;
+  }
+  return w;
+}
+
+// CONS_RECT: amplitude bound (if any) plus a support rectangle; kin says whether
+// the pixel's column lies inside the rectangle.
+template <int CONS>
+__device__ __forceinline__ float2 proj_C_t(float2 w, int gj, int gk, bool kin, const ConsDev& c) {
+  if (CONS == CONS_NONE) return w;
+  if (CONS == CONS_AMP) return proj_amp(w, c.amax);
+  if (CONS == CONS_RECT) {
+    if (!kin || gj < c.j0 || gj >= c.j1) return make_float2(0.f, 0.f);
+    return c.amp ? proj_amp(w, c.amax) : w;
+  }
+  return proj_C(w, gj, gk, c);
+}
+
 // T iterations of Algorithm 2 on one tile, with column-strip ownership.
 //
 // Same contract as fgp_tile (an RW x RH region with a T-pixel halo, only the
@@ -233,18 +259,21 @@ __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const flo
 // warps stacked give RW = 32 WX and RH = PPT WY. q, r and the transient x of the
 // owned pixels stay in registers, so the vertical neighbours of the stencil
 // (r above for L^T, x below for L) come from registers except at the ends of
-// a strip. Shared memory holds only what other threads need: p2 = (r2, s2) of
-// every pixel (left neighbour of L^T), x of every pixel (right and, at strip
-// ends, lower neighbour of L) and p1 = (r1, s1) of each strip's last row (upper
-// neighbour of the next strip). b is re-read through the read-only cache.
-template <int TV, int T, int WX, int WY, int PPT, bool HIST = false>
-__device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, const float* beta, int nsteps,
+// a strip. Shared memory holds what other threads need - p2 = (r2, s2) of every
+// pixel (left neighbour of L^T), x of every pixel (right and, at strip ends,
+// lower neighbour of L), p1 = (r1, s1) of each strip's last row (upper
+// neighbour of the next strip) - and b.
+// EDGE = false is the fast path for regions that lie inside the image away
+// from its last row and column: no per-pixel bounds or edge tests.
+template <int TV, int T, int WX, int WY, int PPT, bool HIST, bool EDGE, int CONS>
+__device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, const float* beta, int nsteps,
                                                bool first) {
   constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH;
   extern __shared__ float4 smem4[];
   float2* P2 = reinterpret_cast<float2*>(smem4);      // R
   float2* X = P2 + R;                                  // R
-  float2* P1B = X + R;                                 // WY * RW
+  float2* Bs = X + R;                                  // R
+  float2* P1B = Bs + R;                                // WY * RW
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int wx = warp % WX, wy = warp / WX;
@@ -252,7 +281,8 @@ __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, con
   const int lj0 = wy * PPT;
   const int gk = k0 - T + lk;
   const int gj0 = j0 - T + lj0;
-  const bool colin = (unsigned)gk < (unsigned)I.n;
+  const bool colin = !EDGE || (unsigned)gk < (unsigned)I.n;
+  const bool kin = gk >= I.C.k0 && gk < I.C.k1;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
 
@@ -263,26 +293,32 @@ __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, con
     const int gj = gj0 + s;
     q[s] = z4;
     r[s] = z4;
-    if (!first && colin && (unsigned)gj < (unsigned)I.m) {
+    float2 bb = z2;
+    if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
       const long long o = (long long)gj * I.n + gk;
-      q[s] = __ldg(I.q_in + o);
-      r[s] = __ldg(I.r_in + o);
+      if (!first) {
+        q[s] = __ldg(I.q_in + o);
+        r[s] = __ldg(I.r_in + o);
+      }
+      bb = __ldg(I.b + (long long)gj * I.ld + gk);
     }
     P2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
+    Bs[(lj0 + s) * RW + lk] = bb;
   }
   P1B[wy * RW + lk] = make_float2(r[PPT - 1].x, r[PPT - 1].y);
   __syncthreads();
 
   const float lam = I.lam;
   const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
-  const bool has_right = lk < RW - 1 && gk < I.n - 1;
+  const bool has_right = lk < RW - 1 && (!EDGE || gk < I.n - 1);
+  const bool strip_bottom_in = lj0 + PPT < RH;
   for (int it = 0; it < nsteps; ++it) {
     // phase 1: x = P_C(b - lam L^T r)
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int gj = gj0 + s;
       x[s] = z2;
-      if (colin && (unsigned)gj < (unsigned)I.m) {
+      if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
         float2 up;
         if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
         else up = wy > 0 ? P1B[(wy - 1) * RW + lk] : z2;
@@ -290,8 +326,8 @@ __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, con
         // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]
         const float dre = r[s].x - up.x + r[s].z - left.x;
         const float dim = r[s].y - up.y + r[s].w - left.y;
-        const float2 bb = __ldg(I.b + (long long)gj * I.ld + gk);
-        x[s] = proj_C(make_float2(bb.x - lam * dre, bb.y - lam * dim), gj, gk, I.C);
+        const float2 bb = Bs[(lj0 + s) * RW + lk];
+        x[s] = proj_C_t<CONS>(make_float2(bb.x - lam * dre, bb.y - lam * dim), gj, gk, kin, I.C);
       }
       X[(lj0 + s) * RW + lk] = x[s];
     }
@@ -301,12 +337,12 @@ __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, con
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int gj = gj0 + s;
-      if (colin && (unsigned)gj < (unsigned)I.m) {
+      if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
         float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-        if (gj < I.m - 1) {
+        if (!EDGE || gj < I.m - 1) {
           float2 xd;
           if (s < PPT - 1) xd = x[s + 1];
-          else xd = (lj0 + s + 1 < RH) ? X[(lj0 + s + 1) * RW + lk] : x[s];
+          else xd = strip_bottom_in ? X[(lj0 + s + 1) * RW + lk] : x[s];
           d1r = x[s].x - xd.x;
           d1i = x[s].y - xd.y;
         }
@@ -333,13 +369,24 @@ __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, con
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int lj = lj0 + s, gj = gj0 + s;
-      if (lj >= T && lj < RH - T && (unsigned)gj < (unsigned)I.m) {
+      if (lj >= T && lj < RH - T && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
         const long long o = (long long)gj * I.n + gk;
         I.q_out[o] = q[s];
         I.r_out[o] = r[s];
       }
     }
   }
+}
+
+// Block-level choice between the fast interior path and the general one.
+template <int TV, int T, int WX, int WY, int PPT, bool HIST, int CONS>
+__device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, const float* beta, int nsteps,
+                                               bool first) {
+  constexpr int RW = 32 * WX, RH = PPT * WY;
+  const int gj0 = j0 - T, gk0 = k0 - T;
+  const bool inside = gj0 >= 0 && gk0 >= 0 && gj0 + RH <= I.m - 1 && gk0 + RW <= I.n - 1;
+  if (inside) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS>(I, j0, k0, beta, nsteps, first);
+  else fgp_strip_body<TV, T, WX, WY, PPT, HIST, true, CONS>(I, j0, k0, beta, nsteps, first);
 }
 
 // Block-wide FP64 sum of NV values; the result is valid in thread 0.

@@ -54,6 +54,15 @@ struct GapParams {
 };
 
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s);
+// Per-TV-type launchers, instantiated one translation unit per type (pass_tv*.cu).
+template <int TV>
+cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);
+// Constraint specialisation (CONS_*) of a constraint descriptor.
+inline int cons_mode(const ConsDev& c) {
+  if (c.sup == 0) return c.amp ? CONS_AMP : CONS_NONE;
+  if (c.sup == 1) return CONS_RECT;
+  return CONS_GEN;
+}
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s);
 // Grid of the fused pass for configuration cfg over an m x n image batch.
 dim3 pass_grid(int cfg, int m, int n, int batch);

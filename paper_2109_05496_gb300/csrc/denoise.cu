@@ -2,7 +2,7 @@
 //
 // Kernels
 //   fgp_pass_kernel   T fused FGP iterations per launch on shared-memory tiles
-//                     (see fgp_tile in ctv_device.cuh).
+//                     (pass_tv.cuh; fgp_tile / fgp_strip_tile in ctv_device.cuh).
 //   fgp_gap_kernel    x = P_C(b - lam L^T q) (Eq. (18)) together with the primal
 //                     value of problem (1), the dual value of App. A (Eq. (30)
 //                     times lam) and their gap, reduced in FP64; its last block
@@ -22,28 +22,6 @@
 #include "ctv_kernels.h"
 
 namespace ctv {
-
-template <int KIND, int TV, int T, int A, int B, int C>
-__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(PassParams p) {
-  using G = CfgGeom<KIND, A, B, C>;
-  const int z = blockIdx.z;
-  if (p.st != nullptr && *(volatile const int*)&p.st[z].stop) return;
-  Img I;
-  I.b = p.b + z * p.b_stride;
-  I.ld = p.ld;
-  I.q_in = p.q_in + z * p.d_stride;
-  I.r_in = p.r_in + z * p.d_stride;
-  I.q_out = p.q_out + z * p.d_stride;
-  I.r_out = p.r_out + z * p.d_stride;
-  I.m = p.m;
-  I.n = p.n;
-  float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
-  I.lam = lam > 0.f ? lam : 0.f;
-  I.alpha = p.alpha;
-  I.C = p.C;
-  run_tile<KIND, TV, T, A, B, C>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta, p.nsteps,
-                                 p.first != 0);
-}
 
 // Grid front end of gap_tile: blockIdx.z is the image of an equally sized batch.
 template <int TV>
@@ -89,37 +67,14 @@ static const Cfg kCfgs[] = {CTV_PASS_CONFIGS(CTV_CFG_ROW)};
 #undef CTV_CFG_ROW
 static const int kNumCfgs = (int)(sizeof(kCfgs) / sizeof(kCfgs[0]));
 
-template <int KIND, int TV, int T, int A, int B, int C>
-static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
-  using G = CfgGeom<KIND, A, B, C>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<KIND, TV, T, A, B, C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  fgp_pass_kernel<KIND, TV, T, A, B, C><<<grid, G::NT, G::SMEM, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int TV>
-static cudaError_t launch_pass_tv(int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
-  switch (cfg) {
-#define CTV_CFG_CASE(id, kind, T, A, B, C) \
-  case id: return launch_pass_t<kind, TV, T, A, B, C>(p, grid, s);
-    CTV_PASS_CONFIGS(CTV_CFG_CASE)
-#undef CTV_CFG_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
+  if (cfg < 0 || cfg >= kNumCfgs) return cudaErrorInvalidValue;
+  const int cons = cons_mode(p.C);
   switch (tv) {
-    case TV1_ISO: return launch_pass_tv<TV1_ISO>(cfg, p, grid, s);
-    case TV1_ANISO: return launch_pass_tv<TV1_ANISO>(cfg, p, grid, s);
-    case TV2_ISO: return launch_pass_tv<TV2_ISO>(cfg, p, grid, s);
-    case TV2_ANISO: return launch_pass_tv<TV2_ANISO>(cfg, p, grid, s);
+    case TV1_ISO: return launch_pass_tv<TV1_ISO>(cfg, cons, p, grid, s);
+    case TV1_ANISO: return launch_pass_tv<TV1_ANISO>(cfg, cons, p, grid, s);
+    case TV2_ISO: return launch_pass_tv<TV2_ISO>(cfg, cons, p, grid, s);
+    case TV2_ANISO: return launch_pass_tv<TV2_ANISO>(cfg, cons, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -148,7 +103,12 @@ int default_config(int m, int n, int iters, int tv) {
     const int t = tuned_config(m, n, tv);
     if (t >= 0) return t;
   }
-  return 2;
+  // measured on GB300 (2048^2, 1024^2, 256^2 phantoms, 200 iterations): column-strip
+  // kernels, 4-6 iterations per pass; small images prefer narrow regions
+  const double px = (double)m * (double)n;
+  if (m <= 0 || n <= 0 || px >= 2048.0 * 1024.0) return 3;
+  if (px >= 256.0 * 1024.0) return 5;
+  return 9;
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -424,6 +384,8 @@ int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
 }
 
 int ctv_num_configs(void) { return ctv::num_configs(); }
+
+int ctv_default_config(int m, int n, int iters, int tv_type) { return ctv::default_config(m, n, iters, tv_type); }
 
 int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads) {
   return ctv::config_info(config, iters_per_pass, region_w, region_h, threads) ? CTV_OK : CTV_EINVAL;

@@ -1,0 +1,79 @@
+// The fused FGP pass kernel over an equally sized batch and its launcher for one
+// TV type; each pass_tv<k>.cu instantiates it for one type so that the many
+// configuration x constraint specialisations compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ctv_configs.cuh"
+#include "ctv_device.cuh"
+#include "ctv_kernels.h"
+
+namespace ctv {
+
+template <int KIND, int TV, int T, int A, int B, int C, int CONS>
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(PassParams p) {
+  using G = CfgGeom<KIND, A, B, C>;
+  const int z = blockIdx.z;
+  if (p.st != nullptr && *(volatile const int*)&p.st[z].stop) return;
+  Img I;
+  I.b = p.b + z * p.b_stride;
+  I.ld = p.ld;
+  I.q_in = p.q_in + z * p.d_stride;
+  I.r_in = p.r_in + z * p.d_stride;
+  I.q_out = p.q_out + z * p.d_stride;
+  I.r_out = p.r_out + z * p.d_stride;
+  I.m = p.m;
+  I.n = p.n;
+  const float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
+  I.lam = lam > 0.f ? lam : 0.f;
+  I.alpha = p.alpha;
+  I.C = p.C;
+  I.r_hist = nullptr;
+  I.hist_plane = 0;
+  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
+                                              p.nsteps, p.first != 0);
+}
+
+template <int KIND, int TV, int T, int A, int B, int C, int CONS>
+static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
+  using G = CfgGeom<KIND, A, B, C>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  fgp_pass_kernel<KIND, TV, T, A, B, C, CONS><<<grid, G::NT, G::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Region kernels (kind 0) use the general constraint path; column-strip kernels
+// (kind 1) are specialised per constraint kind.
+template <int KIND, int TV, int T, int A, int B, int C>
+static cudaError_t launch_pass_cons(int cons, const PassParams& p, dim3 grid, cudaStream_t s) {
+  if constexpr (KIND == 0) {
+    return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, s);
+  } else {
+    switch (cons) {
+      case CONS_NONE: return launch_pass_t<KIND, TV, T, A, B, C, CONS_NONE>(p, grid, s);
+      case CONS_AMP: return launch_pass_t<KIND, TV, T, A, B, C, CONS_AMP>(p, grid, s);
+      case CONS_RECT: return launch_pass_t<KIND, TV, T, A, B, C, CONS_RECT>(p, grid, s);
+      default: return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, s);
+    }
+  }
+}
+
+template <int TV>
+cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s) {
+  switch (cfg) {
+#define CTV_CFG_CASE(id, kind, T, A, B, C) \
+  case id: return launch_pass_cons<kind, TV, T, A, B, C>(cons, p, grid, s);
+    CTV_PASS_CONFIGS(CTV_CFG_CASE)
+#undef CTV_CFG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ctv
