@@ -56,30 +56,35 @@ def read_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_2109_05496_gb300/csrc/ctv_device.cuh", "paper_2109_05496_gb300/csrc/pass_tv.cuh",
-                "paper_2109_05496_gb300/csrc/ctv_configs.cuh"):
+    for rel in ("paper_2109_05496_gb300/csrc/ctv_device.cuh", "paper_2109_05496_gb300/csrc/pass_tv.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(cfg_id: int, units_per_launch: float):
-    """DRAM bytes per launch of the fused pass from the committed ncu summary,
-    scaled to this launch's pixel-iterations; None if the kernel changed since."""
-    path = os.path.join(ROOT, "profiles", "fgp_pass_2048x2048.md")
-    try:
-        lines = open(path).read().splitlines()
-    except OSError:
-        return None
+def profiled_traffic(cfg_geom: str, units_per_launch: float):
+    """DRAM bytes per launch of the fused pass from the committed ncu summaries,
+    scaled to this launch's pixel-iterations; None if the kernel source or the
+    configuration's geometry changed since the counters were taken."""
+    import glob
     want = kernel_source_hash()
-    for ln in lines:
-        if ln.startswith("bench-traffic:"):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for ln in open(path).read().splitlines():
+            if not ln.startswith("bench-traffic:"):
+                continue
             kv = dict(p.split("=", 1) for p in ln.split()[1:])
-            if kv.get("kernel_sha") != want or int(kv.get("config", -2)) != cfg_id:
+            if kv.get("kernel_sha") != want or kv.get("geometry") != cfg_geom:
                 continue
             per_unit = float(kv["dram_bytes_per_launch"]) / float(kv["pixel_iters_per_launch"])
             return per_unit * units_per_launch
     return None
+
+
+def config_geometry(lib, cfg: int) -> str:
+    import ctypes
+    v = [ctypes.c_int() for _ in range(4)]
+    lib.ctv_config_info(cfg, *[ctypes.byref(x) for x in v])
+    return "T%d-%dx%d-%d" % tuple(x.value for x in v)
 
 
 class ClockSampler:
@@ -247,12 +252,10 @@ def main():
     pass_ms, pass_n, units, all_n = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
     lib.ctv_profile_read(ctypes.byref(pass_ms), ctypes.byref(pass_n), ctypes.byref(units), ctypes.byref(all_n))
     lib.ctv_profile_enable(0)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2109_05496_gb300 import dist as pdist
+    ms = pdist.max_over_ranks(ms)
     px_it_step = len(TVS) * M * N * ITERS
-    value = world * args.steps * px_it_step / (ms * 1e-3) / 1e9
+    value = pdist.weak_scaling_value(args.steps * px_it_step, ms, world) / 1e9
 
     # end to end through the public API: pinned host input in, result back to pinned host, every step
     e2e = None
@@ -272,19 +275,15 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * args.steps * px_it_step / (ems * 1e-3) / 1e9, "unit": UNIT,
+        ems = pdist.max_over_ranks(f0.elapsed_time(f1))
+        e2e = {"value": pdist.weak_scaling_value(args.steps * px_it_step, ems, world) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": len(TVS) * M * N * 8}
 
     peak, peak_kind = read_peaks()
     per_launch_units = units.value / max(pass_n.value, 1)
     achieved = ALGO_BYTES_PER_PX_IT * units.value / (pass_ms.value * 1e-3) / 1e9 if pass_ms.value > 0 else None
     cfg_used = args.config if args.config >= 0 else default_config_id(lib)
-    traffic = profiled_traffic(cfg_used, per_launch_units)
+    traffic = profiled_traffic(config_geometry(lib, cfg_used), per_launch_units)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": "fgp_pass_kernel", "peak_source": peak_kind + " (hbm_gbs, copy)",
@@ -352,7 +351,7 @@ def run_other_workload(args, world, rank, local):
         ws = ctv.workspace(1, 256, 256, dev)
         C = ctv.Constraint(amp_max=1.0)
         res = {}
-        for cfg in ([args.config] if args.config >= 0 else [0, 2, 4, 10, 11]):
+        for cfg in ([args.config] if args.config >= 0 else list(range(ctv._lib.load().ctv_num_configs()))):
             opts = ctv.make_opts(100, config=cfg)
             for _ in range(args.warmup):
                 ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)

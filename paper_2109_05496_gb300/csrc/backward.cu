@@ -17,8 +17,8 @@
 //     rbar_k = gbar - lam L what
 // Each segment of ckpt_every iterations is first recomputed from its
 // checkpoint by the fused pass, storing every r_k of the segment, then walked
-// backwards one reverse step per launch (a two-pixel halo: the reverse step
-// reads two stencils deep). All Jacobians are those of the projections, which
+// backwards one reverse step per launch (adj_strip_kernel: a two-pixel halo,
+// since the reverse step reads two stencils deep). All Jacobians are those of the projections, which
 // are symmetric; at a projection's boundary the interior branch (identity) is
 // taken, and the projection onto a radius-0 ball has Jacobian 0.
 #include <cuda_runtime.h>
@@ -119,138 +119,6 @@ struct AdjParams {
   ConsDev C;
 };
 
-template <int TV>
-__global__ void __launch_bounds__(ADJ_NT) adj_step_kernel(AdjParams p) {
-  constexpr int RW = ADJ_RW, RH = ADJ_RH, NT = ADJ_NT, R = RW * RH, PPT = R / NT;
-  __shared__ float4 RE[R];   // r_k, then ebar
-  __shared__ float2 XW[R];   // x, then what
-  __shared__ double red[NT / 32];
-  const int z = blockIdx.z;
-  const long long off = (long long)z * p.px;
-  const float lam = fmaxf(p.lam_dev[z], 0.f);
-  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
-  const int m = p.m, n = p.n;
-  const int gj0 = blockIdx.y * (RH - 4) - 2, gk0 = blockIdx.x * (RW - 4) - 2;
-  const int tid = threadIdx.x;
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  float2 bb[PPT], dd[PPT], ww[PPT];
-  float4 qb[PPT], gb[PPT];
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
-    float4 r = z4, q = z4;
-    float2 b2 = make_float2(0.f, 0.f);
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const long long o = off + (long long)gj * n + gk;
-      if (p.r != nullptr) r = __ldg(p.r + o);
-      b2 = __ldg(p.b + o);
-      if (p.Y != nullptr) {
-        const float4 y = __ldg(p.Y + o);
-        q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
-      }
-      if (p.rbn != nullptr) {
-        const float4 y = __ldg(p.rbn + o);
-        q = f4(q.x + p.rc * y.x, q.y + p.rc * y.y, q.z + p.rc * y.z, q.w + p.rc * y.w);
-      }
-    }
-    RE[i] = r;
-    bb[s] = b2;
-    qb[s] = q;
-  }
-  __syncthreads();
-  // A: d = L^T r, w = b - lam d, x = P_C(w)
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    float2 xv = make_float2(0.f, 0.f);
-    dd[s] = make_float2(0.f, 0.f);
-    ww[s] = make_float2(0.f, 0.f);
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 rc = RE[i];
-      const float4 ru = lj > 0 ? RE[i - RW] : z4;
-      const float4 rl = lk > 0 ? RE[i - 1] : z4;
-      dd[s] = make_float2(rc.x - ru.x + rc.z - rl.z, rc.y - ru.y + rc.w - rl.w);
-      ww[s] = make_float2(bb[s].x - lam * dd[s].x, bb[s].y - lam * dd[s].y);
-      xv = proj_C(ww[s], gj, gk, p.C);
-    }
-    XW[i] = xv;
-  }
-  __syncthreads();
-  // B: e = L x, g = r + e/(8 lam), gbar = J_PS(g)^T qbar, ebar = gbar/(8 lam)
-  double lacc = 0.0;
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    float4 eb = z4;
-    gb[s] = z4;
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float2 xc = XW[i];
-      float e1r = 0.f, e1i = 0.f, e2r = 0.f, e2i = 0.f;
-      if (gj < m - 1 && lj < RH - 1) { const float2 xd = XW[i + RW]; e1r = xc.x - xd.x; e1i = xc.y - xd.y; }
-      if (gk < n - 1 && lk < RW - 1) { const float2 xr = XW[i + 1]; e2r = xc.x - xr.x; e2i = xc.y - xr.y; }
-      const float4 rc = RE[i];
-      const float4 g = f4(rc.x + c8 * e1r, rc.y + c8 * e1i, rc.z + c8 * e2r, rc.w + c8 * e2i);
-      float4 gbar = proj_S_adj<TV>(g, qb[s], p.alpha);
-      if (gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
-      if (gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
-      gb[s] = gbar;
-      eb = f4(c8 * gbar.x, c8 * gbar.y, c8 * gbar.z, c8 * gbar.w);
-      if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2)
-        lacc -= (double)(8.f * c8 * c8) * (double)(gbar.x * e1r + gbar.y * e1i + gbar.z * e2r + gbar.w * e2i);
-    }
-    RE[i] = eb;
-  }
-  __syncthreads();
-  // C: xbar = L^T ebar, what = J_PC(w)^T xbar; bbar += what
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    float2 wh = make_float2(0.f, 0.f);
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 ec = RE[i];
-      const float4 eu = lj > 0 ? RE[i - RW] : z4;
-      const float4 el = lk > 0 ? RE[i - 1] : z4;
-      const float2 xb = make_float2(ec.x - eu.x + ec.z - el.z, ec.y - eu.y + ec.w - el.w);
-      wh = proj_C_adj(ww[s], xb, gj, gk, p.C);
-      if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2) {
-        const long long o = off + (long long)gj * n + gk;
-        float2 acc = p.bbar[o];
-        acc.x += wh.x;
-        acc.y += wh.y;
-        p.bbar[o] = acc;
-        lacc -= (double)(dd[s].x * wh.x + dd[s].y * wh.y);
-      }
-    }
-    XW[i] = wh;
-  }
-  __syncthreads();
-  // D: rbar_k = gbar - lam L what
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    if (lj >= 2 && lj < RH - 2 && lk >= 2 && lk < RW - 2 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float2 wc = XW[i];
-      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-      if (gj < m - 1) { const float2 wd = XW[i + RW]; d1r = wc.x - wd.x; d1i = wc.y - wd.y; }
-      if (gk < n - 1) { const float2 wr = XW[i + 1]; d2r = wc.x - wr.x; d2i = wc.y - wr.y; }
-      p.rb_out[off + (long long)gj * n + gk] =
-          f4(gb[s].x - lam * d1r, gb[s].y - lam * d1i, gb[s].z - lam * d2r, gb[s].w - lam * d2i);
-    }
-  }
-  double v[1] = {lacc};
-  block_sum<NT, 1>(v, red);
-  if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
-}
-
 // Finalize adjoint: region with a one-pixel halo.
 template <int TV>
 __global__ void __launch_bounds__(ADJ_NT) adj_final_kernel(AdjParams p) {
@@ -275,7 +143,7 @@ __global__ void __launch_bounds__(ADJ_NT) adj_final_kernel(AdjParams p) {
     QS[i] = q;
   }
   __syncthreads();
-  double lacc = 0.0;
+  float lacc = 0.f;
 #pragma unroll
   for (int s = 0; s < PPT; ++s) {
     const int i = tid + s * NT;
@@ -293,7 +161,7 @@ __global__ void __launch_bounds__(ADJ_NT) adj_final_kernel(AdjParams p) {
       wh = proj_C_adj(w, __ldg(p.xbar + o), gj, gk, p.C);
       if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1) {
         p.bbar[o] = wh;
-        lacc -= (double)(dr * wh.x + di * wh.y);
+        lacc -= dr * wh.x + di * wh.y;
       }
     }
     XW[i] = wh;
@@ -312,7 +180,7 @@ __global__ void __launch_bounds__(ADJ_NT) adj_final_kernel(AdjParams p) {
       p.qbK[off + (long long)gj * n + gk] = f4(-lam * d1r, -lam * d1i, -lam * d2r, -lam * d2i);
     }
   }
-  double v[1] = {lacc};
+  double v[1] = {(double)lacc};
   block_sum<NT, 1>(v, red);
   if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
 }
@@ -398,15 +266,209 @@ static bool hist_config_ok(int cfg) {
   return false;
 }
 
-static cudaError_t launch_adj_step(int tv, const AdjParams& p, int batch, cudaStream_t s) {
-  dim3 grid((p.n + ADJ_RW - 5) / (ADJ_RW - 4), (p.m + ADJ_RH - 5) / (ADJ_RH - 4), batch);
-  switch (tv) {
-    case TV1_ISO: adj_step_kernel<TV1_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
-    case TV1_ANISO: adj_step_kernel<TV1_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
-    case TV2_ISO: adj_step_kernel<TV2_ISO><<<grid, ADJ_NT, 0, s>>>(p); break;
-    default: adj_step_kernel<TV2_ANISO><<<grid, ADJ_NT, 0, s>>>(p); break;
+// Reverse step with column-strip ownership (same arithmetic as adj_step_kernel):
+// a warp covers 32 columns, each thread PPT consecutive rows of its column, so
+// the vertical neighbours of the four stencil phases come from registers except
+// at strip ends. Region 32 WX x PPT WY with a two-pixel halo.
+template <int TV, int WX, int WY, int PPT, int CONS>
+__global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
+  constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH, NT = 32 * WX * WY;
+  extern __shared__ float2 smf2[];
+  float2* S2 = smf2;          // p2 of r (phase A), then p2 of ebar (phases B-C)
+  float2* XW = S2 + R;        // x (A-B), then what (C-D)
+  float2* B1 = XW + R;        // strip-bottom p1 of r (A), then of ebar (B-C)
+  __shared__ double red[NT / 32];
+  const int z = blockIdx.z;
+  const long long off = (long long)z * p.px;
+  const float lam = fmaxf(p.lam_dev[z], 0.f);
+  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
+  const int m = p.m, n = p.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wx = warp % WX, wy = warp / WX;
+  const int lk = wx * 32 + lane, lj0 = wy * PPT;
+  const int gk = blockIdx.x * (RW - 4) - 2 + lk;
+  const int gj0 = blockIdx.y * (RH - 4) - 2 + lj0;
+  const bool colin = (unsigned)gk < (unsigned)n;
+  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
+  const bool kint = lk >= 2 && lk < RW - 2;
+  const bool right_in = lk < RW - 1 && gk < n - 1;
+  const bool strip_next = lj0 + PPT < RH;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const float2 z2 = make_float2(0.f, 0.f);
+  float4 r[PPT], qb[PPT], gb[PPT];
+  float2 bb[PPT], dd[PPT], ww[PPT], xx[PPT], e1[PPT], e2[PPT], ba[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int gj = gj0 + s;
+    r[s] = z4;
+    qb[s] = z4;
+    bb[s] = z2;
+    ba[s] = z2;
+    if (colin && (unsigned)gj < (unsigned)m) {
+      const long long o = off + (long long)gj * n + gk;
+      if (p.r != nullptr) r[s] = __ldg(p.r + o);
+      bb[s] = __ldg(p.b + o);
+      if (kint && lj0 + s >= 2 && lj0 + s < RH - 2) ba[s] = p.bbar[o];   // running dL/db, updated in phase C
+      float4 q = z4;
+      if (p.Y != nullptr) {
+        const float4 y = __ldg(p.Y + o);
+        q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
+      }
+      if (p.rbn != nullptr) {
+        const float4 y = __ldg(p.rbn + o);
+        q = f4(q.x + p.rc * y.x, q.y + p.rc * y.y, q.z + p.rc * y.z, q.w + p.rc * y.w);
+      }
+      qb[s] = q;
+    }
+    S2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
   }
+  B1[wy * RW + lk] = make_float2(r[PPT - 1].x, r[PPT - 1].y);
+  __syncthreads();
+  // A: d = L^T r, w = b - lam d, x = P_C(w)
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int gj = gj0 + s;
+    dd[s] = z2;
+    ww[s] = z2;
+    xx[s] = z2;
+    if (colin && (unsigned)gj < (unsigned)m) {
+      float2 up;
+      if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
+      else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
+      const float2 left = lk > 0 ? S2[(lj0 + s) * RW + lk - 1] : z2;
+      dd[s] = make_float2(r[s].x - up.x + r[s].z - left.x, r[s].y - up.y + r[s].w - left.y);
+      ww[s] = make_float2(bb[s].x - lam * dd[s].x, bb[s].y - lam * dd[s].y);
+      xx[s] = proj_C_t<CONS>(ww[s], gj, gk, kin, p.C);
+    }
+    XW[(lj0 + s) * RW + lk] = xx[s];
+  }
+  __syncthreads();
+  // B: e = L x, g = r + e/(8 lam), gbar = J_PS(g)^T qbar, ebar = gbar/(8 lam)
+  float lacc = 0.f;
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int gj = gj0 + s;
+    gb[s] = z4;
+    e1[s] = z2;
+    e2[s] = z2;
+    if (colin && (unsigned)gj < (unsigned)m) {
+      float ea = 0.f, eb_ = 0.f, ec = 0.f, ed = 0.f;
+      if (gj < m - 1) {
+        float2 xd;
+        if (s < PPT - 1) xd = xx[s + 1];
+        else xd = strip_next ? XW[(lj0 + s + 1) * RW + lk] : xx[s];
+        ea = xx[s].x - xd.x;
+        eb_ = xx[s].y - xd.y;
+      }
+      if (right_in) {
+        const float2 xr = XW[(lj0 + s) * RW + lk + 1];
+        ec = xx[s].x - xr.x;
+        ed = xx[s].y - xr.y;
+      }
+      const float4 g = f4(r[s].x + c8 * ea, r[s].y + c8 * eb_, r[s].z + c8 * ec, r[s].w + c8 * ed);
+      float4 gbar = proj_S_adj<TV>(g, qb[s], p.alpha);
+      if (gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
+      if (gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
+      gb[s] = gbar;
+      e1[s] = make_float2(c8 * gbar.x, c8 * gbar.y);
+      e2[s] = make_float2(c8 * gbar.z, c8 * gbar.w);
+      const int lj = lj0 + s;
+      if (kint && lj >= 2 && lj < RH - 2)
+        lacc -= 8.f * c8 * c8 * (gbar.x * ea + gbar.y * eb_ + gbar.z * ec + gbar.w * ed);
+    }
+    // phase A's reads of S2 and B1 all happened before the last barrier
+    S2[(lj0 + s) * RW + lk] = e2[s];
+  }
+  B1[wy * RW + lk] = e1[PPT - 1];
+  __syncthreads();
+  // C: xbar = L^T ebar, what = J_PC(w)^T xbar; bbar += what
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int gj = gj0 + s;
+    float2 wh = z2;
+    if (colin && (unsigned)gj < (unsigned)m) {
+      float2 up;
+      if (s > 0) up = e1[s - 1];
+      else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
+      const float2 left = lk > 0 ? S2[(lj0 + s) * RW + lk - 1] : z2;
+      const float2 xb = make_float2(e1[s].x - up.x + e2[s].x - left.x, e1[s].y - up.y + e2[s].y - left.y);
+      wh = proj_C_adj(ww[s], xb, gj, gk, p.C);
+      const int lj = lj0 + s;
+      if (kint && lj >= 2 && lj < RH - 2) {
+        p.bbar[off + (long long)gj * n + gk] = make_float2(ba[s].x + wh.x, ba[s].y + wh.y);
+        lacc -= dd[s].x * wh.x + dd[s].y * wh.y;
+      }
+    }
+    xx[s] = wh;
+    XW[(lj0 + s) * RW + lk] = wh;
+  }
+  __syncthreads();
+  // D: rbar_k = gbar - lam L what
+  if (kint && colin) {
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int lj = lj0 + s, gj = gj0 + s;
+      if (lj >= 2 && lj < RH - 2 && (unsigned)gj < (unsigned)m) {
+        float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+        if (gj < m - 1) {
+          const float2 wd = s < PPT - 1 ? xx[s + 1] : XW[(lj0 + s + 1) * RW + lk];
+          d1r = xx[s].x - wd.x;
+          d1i = xx[s].y - wd.y;
+        }
+        if (gk < n - 1) {
+          const float2 wr = XW[(lj0 + s) * RW + lk + 1];
+          d2r = xx[s].x - wr.x;
+          d2i = xx[s].y - wr.y;
+        }
+        p.rb_out[off + (long long)gj * n + gk] =
+            f4(gb[s].x - lam * d1r, gb[s].y - lam * d1i, gb[s].z - lam * d2r, gb[s].w - lam * d2i);
+      }
+    }
+  }
+  double v[1] = {(double)lacc};
+  block_sum<NT, 1>(v, red);
+  if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
+}
+
+// reverse-step geometry: warps across, warps down, rows per thread
+#ifndef CTV_ADJ_CFG
+#define CTV_ADJ_CFG 3
+#endif
+#if CTV_ADJ_CFG == 1
+constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 4;    // 64 x 32 region, 512 threads
+#elif CTV_ADJ_CFG == 2
+constexpr int AS_WX = 2, AS_WY = 4, AS_PPT = 4;    // 64 x 16 region, 256 threads
+#else
+constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 2;    // 64 x 16 region, 512 threads
+#endif
+
+template <int TV, int CONS>
+static cudaError_t launch_adj_strip_t(const AdjParams& p, int batch, cudaStream_t s) {
+  constexpr int RW = 32 * AS_WX, RH = AS_PPT * AS_WY;
+  constexpr size_t smem = (size_t)RW * RH * 2 * sizeof(float2) + (size_t)AS_WY * RW * sizeof(float2);
+  dim3 grid((p.n + RW - 5) / (RW - 4), (p.m + RH - 5) / (RH - 4), batch);
+  adj_strip_kernel<TV, AS_WX, AS_WY, AS_PPT, CONS><<<grid, 32 * AS_WX * AS_WY, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int TV>
+static cudaError_t launch_adj_strip_tv(int cons, const AdjParams& p, int batch, cudaStream_t s) {
+  switch (cons) {
+    case CONS_NONE: return launch_adj_strip_t<TV, CONS_NONE>(p, batch, s);
+    case CONS_AMP: return launch_adj_strip_t<TV, CONS_AMP>(p, batch, s);
+    case CONS_RECT: return launch_adj_strip_t<TV, CONS_RECT>(p, batch, s);
+    default: return launch_adj_strip_t<TV, CONS_GEN>(p, batch, s);
+  }
+}
+
+static cudaError_t launch_adj_step(int tv, const AdjParams& p, int batch, cudaStream_t s) {
+  const int cons = cons_mode(p.C);
+  switch (tv) {
+    case TV1_ISO: return launch_adj_strip_tv<TV1_ISO>(cons, p, batch, s);
+    case TV1_ANISO: return launch_adj_strip_tv<TV1_ANISO>(cons, p, batch, s);
+    case TV2_ISO: return launch_adj_strip_tv<TV2_ISO>(cons, p, batch, s);
+    default: return launch_adj_strip_tv<TV2_ANISO>(cons, p, batch, s);
+  }
 }
 
 static cudaError_t launch_adj_final(int tv, const AdjParams& p, int batch, cudaStream_t s) {
@@ -467,7 +529,7 @@ static UnrolledLayout layout(char* base, int batch, int m, int n, int K, int ckp
 
 static int unrolled_config(const ctv_opts* o) {
   if (o != nullptr && o->config >= 0 && hist_config_ok(o->config)) return o->config;
-  return 2;
+  return 5;
 }
 
 struct UnrolledArgs {

@@ -414,132 +414,4 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* smem, 
   }
 }
 
-// Evaluation of one image at a dual point q (shared by the finalize step and the
-// duality-gap checks).
-struct GapImg {
-  const float2* b;      // row stride ld
-  int ld;
-  const float4* q;      // dense m x n; nullptr means q = 0
-  float2* x;            // nullable: receives x = P_C(b - lam L^T q), row stride ld
-  float4* q_export;     // nullable: receives q (dense m x n)
-  int m, n;
-  float lam, alpha;
-  ConsDev C;
-};
-
-constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
-
-// One GAP_RW x GAP_RH region with a one-pixel halo; its interior of
-// (GAP_RW - 2) x (GAP_RH - 2) pixels starting at (j0, k0) is evaluated: x at a
-// pixel needs q at the pixel, above and to the left (Eq. (18)); the TV summand
-// needs x below and to the right. Returns, in thread 0, the block's sums of
-//   acc[0] = ||x - b||^2, acc[1] = TV(x), acc[2] = ||b||^2 - ||w||^2 + ||w - P_C(w)||^2
-// (w = b - lam L^T q), i.e. 2 P - 2 lam TV and 2 D of App. A.
-template <int TV>
-__device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4* qs, float2* xs, double* red,
-                                         double (&acc)[3]) {
-  constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
-  const int m = g.m, n = g.n;
-  const int gj0 = j0 - 1, gk0 = k0 - 1;
-  const int tid = threadIdx.x;
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  const float lam = g.lam;
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int gj = gj0 + i / RW, gk = gk0 + i % RW;
-    float4 v = z4;
-    if (g.q != nullptr && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) v = __ldg(g.q + (long long)gj * n + gk);
-    qs[i] = v;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    float2 xv = make_float2(0.f, 0.f);
-    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 qc = qs[i];
-      const float4 qu = lj > 0 ? qs[i - RW] : z4;
-      const float4 ql = lk > 0 ? qs[i - 1] : z4;
-      const float2 bb = __ldg(g.b + (long long)gj * g.ld + gk);
-      xv = proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)),
-                  gj, gk, g.C);
-    }
-    xs[i] = xv;
-  }
-  __syncthreads();
-  acc[0] = acc[1] = acc[2] = 0.0;
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int i = tid + s * NT;
-    const int lj = i / RW, lk = i % RW;
-    const int gj = gj0 + lj, gk = gk0 + lk;
-    if (lj >= 1 && lj < RH - 1 && lk >= 1 && lk < RW - 1 && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
-      const float4 qc = qs[i];
-      const float4 qu = qs[i - RW];
-      const float4 ql = qs[i - 1];
-      const float2 bb = __ldg(g.b + (long long)gj * g.ld + gk);
-      const float dlr = lam * (qc.x - qu.x + qc.z - ql.z);   // lam (L^T q)
-      const float dli = lam * (qc.y - qu.y + qc.w - ql.w);
-      const float wr = bb.x - dlr, wi = bb.y - dli;
-      const float2 xc = xs[i];
-      float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-      if (gj < m - 1) { const float2 xd = xs[i + RW]; d1r = xc.x - xd.x; d1i = xc.y - xd.y; }
-      if (gk < n - 1) { const float2 xr = xs[i + 1]; d2r = xc.x - xr.x; d2i = xc.y - xr.y; }
-      const float er = xc.x - bb.x, ei = xc.y - bb.y;
-      acc[0] += (double)(er * er + ei * ei);
-      acc[1] += (double)tv_term<TV>(d1r, d1i, d2r, d2i, g.alpha);
-      // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
-      const float hr = wr - xc.x, hi = wi - xc.y;
-      acc[2] += (double)(2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (double)(hr * hr + hi * hi);
-      if (g.x != nullptr) g.x[(long long)gj * g.ld + gk] = xc;
-      if (g.q_export != nullptr) g.q_export[(long long)gj * n + gk] = qc;
-    }
-  }
-  block_sum<NT, 3>(acc, red);
-}
-
-// Adds the block sums into st and lets the last block of the reduction turn them
-// into primal, dual and gap, apply the stopping test (checks) or record the final
-// iteration count, and reset the accumulators. Thread 0 holds the block sums.
-__device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3], unsigned nblk, float lam, bool bad_lam,
-                                           int set, int stopped, int iter, double gap_tol, int final_call, int* last) {
-  if (threadIdx.x == 0) {
-    atomicAdd(&st->acc[0], acc[0]);
-    atomicAdd(&st->acc[1], acc[1]);
-    atomicAdd(&st->acc[2], acc[2]);
-    __threadfence();
-    *last = (atomicAdd(&st->blocks_done, 1u) == nblk - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (*last && threadIdx.x == 0) {
-    __threadfence();
-    volatile double* a = st->acc;
-    const double fid = a[0], tvs = a[1], dual2 = a[2];
-    const double P = 0.5 * fid + (double)lam * tvs;
-    const double D = 0.5 * dual2;
-    st->primal = P;
-    st->dual = D;
-    st->gap = P - D;
-    if (bad_lam) st->status = 1;   // CTV_EINVAL
-    if (!final_call) {
-      st->iters = iter;
-      if (gap_tol > 0.0 && P - D <= gap_tol * fmax(P, 1e-30)) {
-        st->stop = 1;
-        st->stop_set = set;
-        st->stop_iter = iter;
-      }
-    } else {
-      st->iters = stopped ? st->stop_iter : iter;
-    }
-    a[0] = 0.0;
-    a[1] = 0.0;
-    a[2] = 0.0;
-    __threadfence();
-    st->blocks_done = 0u;
-  }
-}
-
 }  // namespace ctv

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "ctv_device.cuh"
+#include "gap_device.cuh"
 
 namespace ctv {
 

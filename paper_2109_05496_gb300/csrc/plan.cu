@@ -19,6 +19,7 @@
 #include "ctv.h"
 #include "ctv_configs.cuh"
 #include "ctv_device.cuh"
+#include "gap_device.cuh"
 #include "ctv_host.h"
 
 namespace ctv {
