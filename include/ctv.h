@@ -69,9 +69,12 @@ typedef enum {
 
 /* The closed convex set C of problem (1), a product of per-pixel sets.
  * amp_bound != 0 adds |x| <= amp_max (Eq. (25) with amp_max = 1; projection
- * Eq. (26)). support_kind: 0 none; 1 rectangle rows [rect[0], rect[2]) x
- * columns [rect[1], rect[3]) (x = 0 outside); 2 mask: device uint8 array of
- * m x n bytes, row stride mask_ld, x = 0 where the byte is 0. */
+ * Eq. (26)). box != 0 instead bounds the parts: box_re[0] <= Re x <= box_re[1]
+ * and box_im[0] <= Im x <= box_im[1] (amp_bound and box are exclusive: the
+ * projection onto their intersection is not a composition of the two).
+ * support_kind: 0 none; 1 rectangle rows [rect[0], rect[2]) x columns
+ * [rect[1], rect[3]) (x = 0 outside); 2 mask: device uint8 array of m x n
+ * bytes, row stride mask_ld, x = 0 where the byte is 0. */
 typedef struct {
   int amp_bound;
   float amp_max;
@@ -79,6 +82,9 @@ typedef struct {
   int rect[4];
   const uint8_t* mask;
   int mask_ld;
+  int box;
+  float box_re[2];
+  float box_im[2];
 } ctv_constraint;
 
 /* Solver options.
@@ -89,7 +95,9 @@ typedef struct {
  *             later passes become no-ops on the device (no host synchronisation).
  * alpha       the weight of Eq. (9)/(10), in [0, 1]; ignored by type I.
  * warm_start  nonzero: q_0 = r_1 = the q held in dual_state on entry (t_1 = 1).
- * config      kernel configuration index (see ctv_config_info); -1 picks one.  */
+ * config      kernel configuration index (see ctv_config_info); -1 picks one.
+ * plain_gp    nonzero: the non-accelerated gradient projection of Eq. (21)
+ *             (q_{k+1} = P_S(q_k - grad h(q_k) / (16 lam^2)), no extrapolation). */
 typedef struct {
   int max_iters;
   int check_every;
@@ -97,6 +105,7 @@ typedef struct {
   float alpha;
   int warm_start;
   int config;
+  int plain_gp;
 } ctv_opts;
 
 /* Result statistics of one image. iters: iterations actually run; stopped:
@@ -274,6 +283,19 @@ int ctv_pr_gradient(ctv_pr_plan* plan, const void* z, const float* sqrt_y, const
 int ctv_pr_solve(ctv_pr_plan* plan, const float* sqrt_y, const void* H, float tau, float gamma,
                  const ctv_constraint* C, int tv_type, const ctv_opts* inner, int outer_iters,
                  int accelerate, void* x_io, double* loss_hist, ctv_stream stream);
+
+/* Algorithm 1 / Eq. (14) with the step chosen by backtracking (the paper selects
+ * gamma "via a line search" without details; this is the sufficient-decrease
+ * test of Beck and Teboulle's FISTA): at z_k, starting from the previous step
+ * (gamma0 at k = 0), gamma is multiplied by eta in (0, 1) until
+ * F(x) <= F(z_k) + <x - z_k, grad F(z_k)> + ||x - z_k||^2 / (2 gamma), x being
+ * the prox step from z_k with that gamma (its FGP warm start restored for every
+ * trial). Synchronises `stream` once per trial. gamma_hist: NULL or HOST array
+ * of outer_iters floats receiving the accepted steps; loss_hist as above. */
+int ctv_pr_solve_ls(ctv_pr_plan* plan, const float* sqrt_y, const void* H, float tau, float gamma0,
+                    float eta, const ctv_constraint* C, int tv_type, const ctv_opts* inner,
+                    int outer_iters, int accelerate, void* x_io, double* loss_hist,
+                    float* gamma_hist, ctv_stream stream);
 
 /* One proximal-gradient step for problem (2) with a caller-supplied gradient:
  * v = z - gamma * grad; x_out = prox_{gamma (tau TV + I_C)}(v) by Algorithm 2

@@ -103,18 +103,20 @@ def tv_value_terms(u: np.ndarray, v: np.ndarray, terms) -> float:
     return float(sum(wi * math.sqrt(sum(d[i] ** 2 for i in g)) for g, wi in zip(groups, w)))
 
 
-def _project_C(xu, xv, amp_max, support):
+def _project_C(xu, xv, amp_max, support, box=None):
     if amp_max is not None:
         a = np.sqrt(xu * xu + xv * xv)
         f = amp_max / np.maximum(amp_max, a)
         xu, xv = xu * f, xv * f
+    elif box is not None:
+        xu, xv = np.clip(xu, box[0], box[1]), np.clip(xv, box[2], box[3])
     if support is not None:
         xu, xv = xu * support, xv * support
     return xu, xv
 
 
 def projected_subgradient(bu, bv, lam, terms, amp_max=None, support=None,
-                          iters=200000, step0=None):
+                          iters=200000, step0=None, box=None):
     """Minimise 1/2||x - b||^2 + lam TV(x) over C with a projected subgradient
     method (steps c/sqrt(k)), returning the best iterate found. Uses only the
     term-list TV and the projection onto C."""
@@ -131,7 +133,7 @@ def projected_subgradient(bu, bv, lam, terms, amp_max=None, support=None,
 
     def proj(x):
         xu, xv = x[: m * n].reshape(m, n), x[m * n:].reshape(m, n)
-        pu, pv = _project_C(xu, xv, amp_max, None if sup is None else support.astype(float))
+        pu, pv = _project_C(xu, xv, amp_max, None if sup is None else support.astype(float), box)
         return np.concatenate([pu.ravel(), pv.ravel()])
 
     def obj(x):

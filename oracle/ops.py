@@ -130,12 +130,15 @@ class Constraint:
     """The closed convex set C of problem (1) as a product of per-pixel sets.
 
     amp_max: None for no bound, else |x| <= amp_max (Eq. (25) uses 1).
+    box:     None, or (re_lo, re_hi, im_lo, im_hi) bounds on Re x and Im x
+             (used without amp_max: each part is then projected independently).
     rect:    None, or (j0, k0, j1, k1): x = 0 outside rows [j0, j1) x cols [k0, k1).
     mask:    None, or a bool m x n tensor: x = 0 where mask is False.
     """
     amp_max: Optional[float] = 1.0
     rect: Optional[Tuple[int, int, int, int]] = None
     mask: Optional[torch.Tensor] = None
+    box: Optional[Tuple[float, float, float, float]] = None
 
     def support(self, m: int, n: int) -> Optional[torch.Tensor]:
         s = None
@@ -169,6 +172,9 @@ def P_C(u, v, C: Optional[Constraint]):
     if C.amp_max is not None:
         f = _scale_into_ball(u * u + v * v, float(C.amp_max))
         u, v = u * f, v * f
+    elif C.box is not None:
+        lo_r, hi_r, lo_i, hi_i = (float(t) for t in C.box)
+        u, v = torch.clamp(u, lo_r, hi_r), torch.clamp(v, lo_i, hi_i)
     s = C.support(u.shape[0], u.shape[1])
     if s is not None:
         z = torch.zeros_like(u)

@@ -106,3 +106,44 @@ def fista_pr(x0, sqrt_y, H, tau: float, gamma: float, outer: int, inner: int = 1
             z = x
         x_prev = x
     return x_prev, losses
+
+
+def fista_pr_ls(x0, sqrt_y, H, tau: float, gamma0: float, eta: float, outer: int, inner: int = 10,
+                tv_type: str = "tv1_aniso", alpha: float = 0.5, C: Optional[Constraint] = None,
+                accelerate: bool = True, max_trials: int = 60):
+    """Algorithm 1 (or Eq. (14)) with the step chosen by backtracking: starting from
+    the previous step, gamma <- eta * gamma until
+        F(x) <= F(z) + <x - z, grad F(z)> + ||x - z||^2 / (2 gamma),
+    x being the prox step from z with that gamma (the FGP warm start is the
+    previous outer iteration's dual for every trial). Returns (x_K, gammas)."""
+    x0 = torch.as_tensor(x0).to(CT)
+    sqrt_y = torch.as_tensor(sqrt_y).to(DT)
+    H = torch.as_tensor(H).to(CT)
+    z = x0.clone()
+    x_prev = x0.clone()
+    t = 1.0
+    q = None
+    gamma = float(gamma0)
+    gammas = []
+    for _ in range(outer):
+        Fz = fidelity(z, sqrt_y, H)
+        g = fidelity_grad(z, sqrt_y, H)
+        for _trial in range(max_trials):
+            v = z - gamma * g
+            res = fgp((v.real.clone(), v.imag.clone()), tau * gamma, inner, tv_type, alpha, C, q0=q)
+            x = torch.complex(res.x[0], res.x[1])
+            d = x - z
+            rhs = Fz + float((d.real * g.real + d.imag * g.imag).sum()) + float((d.abs() ** 2).sum()) / (2 * gamma)
+            if fidelity(x, sqrt_y, H) <= rhs:
+                break
+            gamma *= eta
+        gammas.append(gamma)
+        q = res.q
+        if accelerate:
+            t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+            z = x + ((t - 1.0) / t_next) * (x - x_prev)
+            t = t_next
+        else:
+            z = x
+        x_prev = x
+    return x_prev, gammas

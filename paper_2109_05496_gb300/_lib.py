@@ -20,12 +20,13 @@ c_int, c_float, c_double, c_size_t, c_void_p, c_longlong = C.c_int, C.c_float, C
 
 class CtvConstraint(C.Structure):
     _fields_ = [("amp_bound", c_int), ("amp_max", c_float), ("support_kind", c_int),
-                ("rect", c_int * 4), ("mask", c_void_p), ("mask_ld", c_int)]
+                ("rect", c_int * 4), ("mask", c_void_p), ("mask_ld", c_int),
+                ("box", c_int), ("box_re", c_float * 2), ("box_im", c_float * 2)]
 
 
 class CtvOpts(C.Structure):
     _fields_ = [("max_iters", c_int), ("check_every", c_int), ("gap_tol", c_double),
-                ("alpha", c_float), ("warm_start", c_int), ("config", c_int)]
+                ("alpha", c_float), ("warm_start", c_int), ("config", c_int), ("plain_gp", c_int)]
 
 
 class CtvStats(C.Structure):
@@ -42,7 +43,7 @@ class CtvImageDesc(C.Structure):
                 ("lam", c_float), ("alpha", c_float), ("tv_type", c_int), ("C", CtvConstraint)]
 
 
-assert C.sizeof(CtvConstraint) == 48 and C.sizeof(CtvOpts) == 32 and C.sizeof(CtvStats) == 40
+assert C.sizeof(CtvConstraint) == 64 and C.sizeof(CtvOpts) == 32 and C.sizeof(CtvStats) == 40
 
 
 P = C.POINTER
@@ -81,6 +82,8 @@ SIGNATURES = {
     "ctv_pr_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ctv_pr_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, P(CtvConstraint), c_int,
                              P(CtvOpts), c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "ctv_pr_solve_ls": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, c_float, P(CtvConstraint), c_int,
+                                P(CtvOpts), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ctv_prox_grad_workspace_size": (c_size_t, [c_int, c_int]),
     "ctv_prox_grad_step": (c_int, [c_void_p, c_void_p, c_float, c_float, P(CtvConstraint), c_int, P(CtvOpts),
                                    c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int, c_int, c_void_p,

@@ -28,16 +28,21 @@ def tv_code(tv: Union[str, int]) -> int:
 @dataclass
 class Constraint:
     """The set C of problem (1): |x| <= amp_max (None: no bound; Eq. (25) uses 1),
-    an optional support rectangle (j0, k0, j1, k1) (half-open) or a support mask
-    (CUDA uint8/bool tensor, nonzero = inside)."""
+    or a box (re_lo, re_hi, im_lo, im_hi) on the real and imaginary parts (give
+    amp_max=None with it), and an optional support rectangle (j0, k0, j1, k1)
+    (half-open) or support mask (CUDA uint8/bool tensor, nonzero = inside)."""
     amp_max: Optional[float] = 1.0
     rect: Optional[Tuple[int, int, int, int]] = None
     mask: Optional[torch.Tensor] = None
+    box: Optional[Tuple[float, float, float, float]] = None
 
     def to_c(self) -> Tuple[L.CtvConstraint, object]:
         c = L.CtvConstraint()
         if self.amp_max is not None:
             c.amp_bound, c.amp_max = 1, float(self.amp_max)
+        if self.box is not None:
+            c.box = 1
+            c.box_re[0], c.box_re[1], c.box_im[0], c.box_im[1] = (float(v) for v in self.box)
         keep = None
         if self.rect is not None:
             c.support_kind = 1
@@ -63,10 +68,11 @@ def _stream_ptr(stream=None) -> int:
 
 
 def make_opts(iters: int, check_every: int = 0, gap_tol: float = 0.0, alpha: float = 0.5,
-              warm_start: bool = False, config: int = -1) -> L.CtvOpts:
+              warm_start: bool = False, config: int = -1, plain_gp: bool = False) -> L.CtvOpts:
     o = L.CtvOpts()
     o.max_iters, o.check_every, o.gap_tol = int(iters), int(check_every), float(gap_tol)
     o.alpha, o.warm_start, o.config = float(alpha), int(bool(warm_start)), int(config)
+    o.plain_gp = int(bool(plain_gp))
     return o
 
 
@@ -150,12 +156,14 @@ def C_ref(obj):
 def denoise(b: torch.Tensor, lam, tv: Union[str, int] = "tv1_iso", iters: int = 100,
             C: Optional[Constraint] = Constraint(), alpha: float = 0.5, check_every: int = 0,
             gap_tol: float = 0.0, dual_state: Optional[torch.Tensor] = None, warm_start: bool = False,
-            config: int = -1, return_stats: bool = False, out: Optional[torch.Tensor] = None):
+            config: int = -1, return_stats: bool = False, out: Optional[torch.Tensor] = None,
+            plain_gp: bool = False):
     """Solve problem (1) for one complex64 image (m, n) or a batch (B, m, n).
 
     lam: a float, or for a batch a float / CUDA float32 tensor of B values.
+    plain_gp: run the gradient projection of Eq. (21) instead of Algorithm 2.
     Returns x (and the statistics when return_stats)."""
-    opts = make_opts(iters, check_every, gap_tol, alpha, warm_start, config)
+    opts = make_opts(iters, check_every, gap_tol, alpha, warm_start, config, plain_gp)
     x = out if out is not None else torch.empty_like(b)
     if b.dim() == 2:
         st = ctv_denoise(b, x, float(lam), C, tv, opts, dual_state, want_stats=return_stats)
@@ -244,6 +252,38 @@ class PRPlan:
                                                        _stream_ptr(stream)))
         del keep
         return (x, hist[:outer_iters]) if return_loss else x
+
+    solve_ls = None   # bound below
+
+
+def _solve_ls(self, x0: torch.Tensor, sqrt_y: torch.Tensor, H: torch.Tensor, tau: float, gamma0: float = 1.0,
+              eta: float = 0.5, C: Optional[Constraint] = Constraint(), tv: Union[str, int] = "tv1_aniso",
+              inner_iters: int = 10, outer_iters: int = 300, alpha: float = 0.5, accelerate: bool = True,
+              config: int = -1, stream=None):
+    """Algorithm 1 (or ISTA) with backtracking on the step (C call ctv_pr_solve_ls).
+    Returns (x_K, F(z_k) per outer iteration, accepted steps)."""
+    self._check(x0, sqrt_y, H)
+    x = x0.clone()
+    hist = torch.zeros(max(outer_iters, 1), dtype=torch.float64, device=x0.device)
+    gam = (L.c_float * max(outer_iters, 1))()
+    cc, keep = (C or NO_CONSTRAINT).to_c()
+    opts = make_opts(inner_iters, 0, 0.0, alpha, False, config)
+    L.check("ctv_pr_solve_ls", self._lib.ctv_pr_solve_ls(
+        self.handle, sqrt_y.data_ptr(), H.data_ptr(), float(tau), float(gamma0), float(eta), C_ref(cc),
+        tv_code(tv), C_ref(opts), int(outer_iters), int(bool(accelerate)), x.data_ptr(), hist.data_ptr(), gam,
+        _stream_ptr(stream)))
+    del keep
+    return x, hist[:outer_iters], list(gam)[:outer_iters]
+
+
+def ip_solve(plan: "PRPlan", x0: torch.Tensor, sqrt_y: torch.Tensor, H: torch.Tensor, outer_iters: int,
+             C: Optional[Constraint] = Constraint(), return_loss: bool = False):
+    """The iterative-projection comparator of Sec. VI-A: x <- P_C(x - grad F(x))
+    (for a unitary propagator this is P_C(A^*(sqrt(y) A x / |A x|)), alternating
+    projections onto the measured modulus and onto C). It is ISTA with tau = 0 and
+    gamma = 1, so it runs through ctv_pr_solve."""
+    return plan.solve(x0, sqrt_y, H, 0.0, 1.0, C, "tv1_aniso", 1, outer_iters, accelerate=False,
+                      return_loss=return_loss)
 
 
 def ctv_prox_grad_step(z: torch.Tensor, grad: torch.Tensor, gamma: float, tau: float, C: Optional[Constraint],
@@ -390,3 +430,6 @@ def denoise_unrolled(b: torch.Tensor, lams, tv: Union[str, int] = "tv1_iso", ite
     lams = lams.to(device=b.device, dtype=torch.float32).reshape(-1)
     x = UnrolledFGP.apply(bb, lams, tv, iters, C, alpha, ckpt_every, config)
     return x.squeeze(0) if squeeze else x
+
+
+PRPlan.solve_ls = _solve_ls

@@ -52,6 +52,9 @@ __device__ __forceinline__ float2 proj_C_adj(float2 w, float2 xb, int gj, int gk
       const float s = c.amax * inv;
       return make_float2(s * (xb.x - nx * dot), s * (xb.y - ny * dot));
     }
+  } else if (c.box) {
+    if (w.x < c.re_lo || w.x > c.re_hi) xb.x = 0.f;
+    if (w.y < c.im_lo || w.y > c.im_hi) xb.y = 0.f;
   }
   return xb;
 }
@@ -547,7 +550,7 @@ struct UnrolledArgs {
 static ctv_status check_unrolled(const UnrolledArgs& a, ConsDev* C) {
   if (a.b == nullptr || a.lams == nullptr || a.ws == nullptr || a.opts == nullptr) return CTV_EINVAL;
   if (a.batch <= 0 || a.batch > 65535 || a.m <= 0 || a.n <= 0) return CTV_EINVAL;
-  if (a.opts->max_iters < 1 || a.ckpt < 1 || a.opts->warm_start) return CTV_EINVAL;
+  if (a.opts->max_iters < 1 || a.ckpt < 1 || a.opts->warm_start || a.opts->plain_gp) return CTV_EINVAL;
   if (!(a.opts->alpha >= 0.f && a.opts->alpha <= 1.f)) return CTV_EINVAL;
   if (a.tv < 0 || a.tv > 3) return CTV_EINVAL;
   if (((uintptr_t)a.b & 7) || ((uintptr_t)a.ws & 255)) return CTV_EINVAL;

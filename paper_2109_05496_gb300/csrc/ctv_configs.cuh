@@ -20,7 +20,11 @@
   X(7, 1, 3, 2, 8, 4)        \
   X(8, 1, 6, 4, 4, 8)        \
   X(9, 1, 4, 1, 4, 8)        \
-  X(10, 1, 2, 1, 4, 8)
+  X(10, 1, 2, 1, 4, 8)       \
+  X(11, 1, 4, 2, 8, 4)       \
+  X(12, 1, 2, 2, 8, 4)       \
+  X(13, 1, 4, 2, 16, 4)      \
+  X(14, 1, 6, 2, 16, 4)
 
 namespace ctv {
 

@@ -24,6 +24,8 @@ struct ConsDev {
   int j0, k0, j1, k1;
   const uint8_t* mask;
   int mask_ld;
+  int box;          // nonzero: re_lo <= Re x <= re_hi, im_lo <= Im x <= im_hi
+  float re_lo, re_hi, im_lo, im_hi;
 };
 
 // Per-image solver record, kept in the caller's workspace.
@@ -40,8 +42,8 @@ struct DevStats {
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 
-// P_C: support first (x = 0 outside), then the amplitude bound of Eq. (26):
-// x * amax / max{amax, |x|}.
+// P_C: support first (x = 0 outside), then the amplitude bound of Eq. (26),
+// x * amax / max{amax, |x|}, or the box on the real and imaginary parts.
 __device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev& c) {
   if (c.sup == 1) {
     if (gj < c.j0 || gj >= c.j1 || gk < c.k0 || gk >= c.k1) return make_float2(0.f, 0.f);
@@ -55,13 +57,35 @@ __device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev
       w.x *= s;
       w.y *= s;
     }
+  } else if (c.box) {
+    w.x = fminf(fmaxf(w.x, c.re_lo), c.re_hi);
+    w.y = fminf(fmaxf(w.y, c.im_lo), c.im_hi);
   }
   return w;
 }
 
 // P_S for the four TV types. g = (r1, s1, r2, s2).
+#ifndef CTV_BRANCHLESS_PS
+#define CTV_BRANCHLESS_PS 1
+#endif
+
 template <int TV>
 __device__ __forceinline__ float4 proj_S(float4 g, float alpha) {
+#if CTV_BRANCHLESS_PS
+  // Same values as below: min{1, radius / |g|} is exactly 1 inside the ball.
+  if (TV == TV1_ISO) {
+    const float s = fminf(1.f, rsqrtf(g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w));
+    return f4(g.x * s, g.y * s, g.z * s, g.w * s);
+  } else if (TV == TV1_ANISO) {
+    const float s1 = fminf(1.f, rsqrtf(g.x * g.x + g.y * g.y));
+    const float s2 = fminf(1.f, rsqrtf(g.z * g.z + g.w * g.w));
+    return f4(g.x * s1, g.y * s1, g.z * s2, g.w * s2);
+  } else if (TV == TV2_ISO) {
+    const float sr = fminf(1.f, alpha * rsqrtf(g.x * g.x + g.z * g.z));
+    const float si = fminf(1.f, (1.f - alpha) * rsqrtf(g.y * g.y + g.w * g.w));
+    return f4(g.x * sr, g.y * si, g.z * sr, g.w * si);
+  }
+#endif
   if (TV == TV1_ISO) {            // Eq. (20): joint 4-vector into the unit ball
     const float nn = g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w;
     if (nn > 1.f) {
@@ -313,10 +337,19 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
   const bool has_right = lk < RW - 1 && (!EDGE || gk < I.n - 1);
   const bool strip_bottom_in = lj0 + PPT < RH;
   for (int it = 0; it < nsteps; ++it) {
+    // Rows whose values can still reach the interior after the remaining steps:
+    // step it must produce q, r on rows [lo, RH - lo) and x on one more row.
+    // With few rows per thread the rows outside are skipped (a warp-uniform
+    // test, since a warp's rows share lj0); with PPT = 8 the per-row branches
+    // cost more instruction-level parallelism than the skipped rows save.
+    constexpr bool SKIP_ROWS = PPT <= 4;
+    const int lo = SKIP_ROWS ? T - (nsteps - 1 - it) : 0;
+    const int hi = SKIP_ROWS ? RH - lo : RH;
     // phase 1: x = P_C(b - lam L^T r)
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int gj = gj0 + s;
+      if (SKIP_ROWS && (lj0 + s < lo || lj0 + s > hi)) continue;
       x[s] = z2;
       if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
         float2 up;
@@ -337,6 +370,7 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int gj = gj0 + s;
+      if (SKIP_ROWS && (lj0 + s < lo || lj0 + s >= hi)) continue;
       if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
         float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
         if (!EDGE || gj < I.m - 1) {

@@ -60,6 +60,7 @@ template <int TV>
 cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);
 // Constraint specialisation (CONS_*) of a constraint descriptor.
 inline int cons_mode(const ConsDev& c) {
+  if (c.box) return CONS_GEN;
   if (c.sup == 0) return c.amp ? CONS_AMP : CONS_NONE;
   if (c.sup == 1) return CONS_RECT;
   return CONS_GEN;

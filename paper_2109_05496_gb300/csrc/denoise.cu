@@ -13,6 +13,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ctv.h"
@@ -104,12 +105,13 @@ int default_config(int m, int n, int iters, int tv) {
     const int t = tuned_config(m, n, tv);
     if (t >= 0) return t;
   }
-  // measured on GB300 (2048^2, 1024^2, 256^2 phantoms, 200 iterations): column-strip
-  // kernels, 4-6 iterations per pass; small images prefer narrow regions
+  // measured on GB300 (2048^2, 1024^2 and 256^2 phantoms, 200 iterations, all four
+  // TV types): column-strip kernels with 4 rows per thread (two 512-thread blocks
+  // per SM); 4 iterations per 64 x 32 region at 2048^2 and 256^2, 6 per 64 x 64
+  // region around 1024^2
   const double px = (double)m * (double)n;
-  if (m <= 0 || n <= 0 || px >= 2048.0 * 1024.0) return 3;
-  if (px >= 256.0 * 1024.0) return 5;
-  return 9;
+  if (m > 0 && n > 0 && px >= 512.0 * 512.0 && px < 1536.0 * 1536.0) return 14;
+  return 11;
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -127,6 +129,15 @@ bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out) {
     if (!(C->amp_max >= 0.f) || isinf(C->amp_max)) return false;
     out->amp = 1;
     out->amax = C->amp_max;
+  }
+  if (C->box) {
+    if (C->amp_bound) return false;
+    if (!(C->box_re[0] <= C->box_re[1]) || !(C->box_im[0] <= C->box_im[1])) return false;
+    out->box = 1;
+    out->re_lo = C->box_re[0];
+    out->re_hi = C->box_re[1];
+    out->im_lo = C->box_im[0];
+    out->im_hi = C->box_im[1];
   }
   if (C->support_kind == 1) {
     out->sup = 1;
@@ -219,6 +230,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
   if (K > 0 && !lam_zero) {
     std::vector<double> beta;
     nesterov_betas(K, &beta);
+    if (o != nullptr && o->plain_gp) std::fill(beta.begin(), beta.end(), 0.0);   // Eq. (21): r_{k+1} = q_k
     PassParams p;
     memset(&p, 0, sizeof(p));
     p.b = (const float2*)c.b;

@@ -238,6 +238,7 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   *out = nullptr;
   if (descs == nullptr || count <= 0 || opts == nullptr) return CTV_EINVAL;
   if (opts->max_iters < 0 || opts->check_every < 0 || !(opts->gap_tol >= 0.0) || opts->warm_start) return CTV_EINVAL;
+  if (opts->plain_gp) return CTV_EUNSUPPORTED;
   int cfg = opts->config;
   if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
   if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1);

@@ -108,6 +108,29 @@ __global__ void pr_fista(const float2* __restrict__ X, const float2* __restrict_
   Z[(long long)j * ldZ + k] = make_float2(x.x + beta * (x.x - xp.x), x.y + beta * (x.y - xp.y));
 }
 
+// Sufficient-decrease terms of the backtracking line search:
+// acc[0] += <x - z, g> (real-pair inner product), acc[1] += ||x - z||^2.
+__global__ void __launch_bounds__(PR_NT) pr_ls_terms(const float2* __restrict__ X, int ldX, const float2* __restrict__ Z,
+                                                     int ldZ, const float2* __restrict__ G, int ldG, int m, int n,
+                                                     double* acc) {
+  __shared__ double red[2 * (PR_NT / 32)];
+  const int j = blockIdx.y, k = blockIdx.x * PR_NT + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (k < n) {
+    const float2 x = X[(long long)j * ldX + k];
+    const float2 z = Z[(long long)j * ldZ + k];
+    const float2 g = G[(long long)j * ldG + k];
+    const float dx = x.x - z.x, dy = x.y - z.y;
+    v[0] = (double)(dx * g.x + dy * g.y);
+    v[1] = (double)(dx * dx + dy * dy);
+  }
+  block_sum<PR_NT, 2>(v, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(acc, v[0]);
+    atomicAdd(acc + 1, v[1]);
+  }
+}
+
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace ctv
@@ -125,16 +148,20 @@ struct ctv_pr_plan {
   float4* dual;      // m x n: FGP dual, warm start across outer iterations
   void* fgp_ws;
   size_t fgp_ws_bytes;
-  double* loss;      // scratch FP64 accumulator
+  double* loss;      // scratch FP64 accumulators (4)
+  float2* Gz;        // m x n: grad F(z_k), kept across line-search trials
+  float4* dual_keep; // m x n: warm-start dual restored before every trial
 };
 
 namespace ctv {
 
-static ctv_status pr_forward_residual(ctv_pr_plan* p, const float* sqrt_y, const float2* H, double* loss_acc,
-                                      cudaStream_t s) {
+// F(z) for the padded field src (object in its corner): FFT, H, IFFT, then the
+// residual g = (xi/|xi|)(|xi| - sqrt(y)) into Q's corner and 1/2 sum (|xi| - sqrt(y))^2.
+static ctv_status pr_forward_loss(ctv_pr_plan* p, const float2* src, const float* sqrt_y, const float2* H,
+                                  double* loss_acc, cudaStream_t s) {
   const long long MN = (long long)p->M * p->N;
   const float inv = 1.0f / (float)MN;
-  if (cufftExecC2C(p->fft, (cufftComplex*)p->P, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (cufftExecC2C(p->fft, (cufftComplex*)src, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS) return CTV_ECUDA;
   if ((MN & 1) == 0) {
     pr_mul_h<<<152 * 8, 256, 0, s>>>((float4*)p->F, (const float4*)H, MN / 2, 0);
   } else {
@@ -145,6 +172,12 @@ static ctv_status pr_forward_residual(ctv_pr_plan* p, const float* sqrt_y, const
   dim3 g((p->n + PR_NT - 1) / PR_NT, p->m);
   pr_residual<<<g, PR_NT, 0, s>>>(p->F, p->N, p->m, p->n, inv, sqrt_y, p->n, p->Q, p->N, loss_acc);
   count_launch();
+  return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
+}
+
+// A^* of the residual held in Q: FFT, conj(H), IFFT; grad F = (1/(MN)) F's corner.
+static ctv_status pr_adjoint(ctv_pr_plan* p, const float2* H, cudaStream_t s) {
+  const long long MN = (long long)p->M * p->N;
   if (cufftExecC2C(p->fft, (cufftComplex*)p->Q, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS) return CTV_ECUDA;
   if ((MN & 1) == 0) {
     pr_mul_h<<<152 * 8, 256, 0, s>>>((float4*)p->F, (const float4*)H, MN / 2, 1);
@@ -154,6 +187,13 @@ static ctv_status pr_forward_residual(ctv_pr_plan* p, const float* sqrt_y, const
   count_launch();
   if (cufftExecC2C(p->fft, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_INVERSE) != CUFFT_SUCCESS) return CTV_ECUDA;
   return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
+}
+
+static ctv_status pr_forward_residual(ctv_pr_plan* p, const float* sqrt_y, const float2* H, double* loss_acc,
+                                      cudaStream_t s) {
+  ctv_status st = pr_forward_loss(p, p->P, sqrt_y, H, loss_acc, s);
+  if (st != CTV_OK) return st;
+  return pr_adjoint(p, H, s);
 }
 
 }  // namespace ctv
@@ -173,7 +213,7 @@ int ctv_pr_plan_create(int m, int n, int M, int N, ctv_pr_plan** out) {
   const size_t small = al256((size_t)m * n * sizeof(float2));
   const size_t dual = al256((size_t)m * n * sizeof(float4));
   p->fgp_ws_bytes = denoise_workspace_bytes(1, m, n);
-  p->bytes = 3 * big + 3 * small + dual + al256(p->fgp_ws_bytes) + 256;
+  p->bytes = 3 * big + 4 * small + 2 * dual + al256(p->fgp_ws_bytes) + 256;
   if (cudaMalloc(&p->base, p->bytes) != cudaSuccess) { delete p; return CTV_ENOMEM; }
   char* c = p->base;
   p->P = (float2*)c; c += big;
@@ -184,6 +224,8 @@ int ctv_pr_plan_create(int m, int n, int M, int N, ctv_pr_plan** out) {
   p->V = (float2*)c; c += small;
   p->dual = (float4*)c; c += dual;
   p->fgp_ws = c; c += al256(p->fgp_ws_bytes);
+  p->Gz = (float2*)c; c += small;
+  p->dual_keep = (float4*)c; c += dual;
   p->loss = (double*)c;
   if (cudaMemset(p->base, 0, p->bytes) != cudaSuccess) { cudaFree(p->base); delete p; return CTV_ECUDA; }
   if (cufftPlan2d(&p->fft, M, N, CUFFT_C2C) != CUFFT_SUCCESS) { cudaFree(p->base); delete p; return CTV_ENOMEM; }
@@ -266,6 +308,94 @@ int ctv_pr_solve(ctv_pr_plan* p, const float* sqrt_y, const void* H, float tau, 
     cur ^= 1;
   }
   // the last x_k sits in X[cur ^ 1]
+  pr_copy<<<g, 256, 0, s>>>(p->X[cur ^ 1], n, (float2*)x_io, n, m, n);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
+}
+
+int ctv_pr_solve_ls(ctv_pr_plan* p, const float* sqrt_y, const void* H, float tau, float gamma0, float eta,
+                    const ctv_constraint* C, int tv_type, const ctv_opts* inner, int outer_iters, int accelerate,
+                    void* x_io, double* loss_hist, float* gamma_hist, ctv_stream stream) {
+  using namespace ctv;
+  if (p == nullptr || sqrt_y == nullptr || H == nullptr || x_io == nullptr || inner == nullptr) return CTV_EINVAL;
+  if (((uintptr_t)H & 15) || ((uintptr_t)x_io & 7)) return CTV_EINVAL;
+  if (!(tau >= 0.f) || !(gamma0 > 0.f) || isinf(tau) || isinf(gamma0) || !(eta > 0.f && eta < 1.f) || outer_iters < 0)
+    return CTV_EINVAL;
+  if (tv_type < 0 || tv_type > 3) return CTV_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return CTV_ECUDA;
+  const int m = p->m, n = p->n;
+  dim3 g((n + 255) / 256, m);
+  dim3 gr((n + PR_NT - 1) / PR_NT, m);
+  const float inv = 1.0f / ((float)p->M * (float)p->N);
+  pr_copy<<<g, 256, 0, s>>>((const float2*)x_io, n, p->P, p->N, m, n);
+  pr_copy<<<g, 256, 0, s>>>((const float2*)x_io, n, p->X[1], n, m, n);
+  count_launch();
+  count_launch();
+  if (loss_hist != nullptr && outer_iters > 0 &&
+      cudaMemsetAsync(loss_hist, 0, sizeof(double) * (size_t)outer_iters, s) != cudaSuccess)
+    return CTV_ECUDA;
+  double t = 1.0;
+  float gamma = gamma0;
+  int cur = 0;
+  ctv_opts o = *inner;
+  for (int k = 0; k < outer_iters; ++k) {
+    // F(z_k) and grad F(z_k)
+    if (cudaMemsetAsync(p->loss, 0, 4 * sizeof(double), s) != cudaSuccess) return CTV_ECUDA;
+    ctv_status st = pr_forward_loss(p, p->P, sqrt_y, (const float2*)H, p->loss, s);
+    if (st != CTV_OK) return st;
+    st = pr_adjoint(p, (const float2*)H, s);
+    if (st != CTV_OK) return st;
+    pr_crop_scale<<<g, 256, 0, s>>>(p->F, p->N, inv, p->Gz, n, m, n);
+    count_launch();
+    if (loss_hist != nullptr && cudaMemcpyAsync(loss_hist + k, p->loss, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return CTV_ECUDA;
+    if (k > 0 && cudaMemcpyAsync(p->dual_keep, p->dual, (size_t)m * n * sizeof(float4), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return CTV_ECUDA;
+    bool accepted = false;
+    for (int trial = 0; trial < 60 && !accepted; ++trial) {
+      if (trial > 0 && k > 0 &&
+          cudaMemcpyAsync(p->dual, p->dual_keep, (size_t)m * n * sizeof(float4), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return CTV_ECUDA;
+      pr_form_v<<<g, 256, 0, s>>>(p->P, p->N, p->Gz, n, gamma, p->V, n, m, n);
+      count_launch();
+      o.warm_start = k > 0 ? 1 : 0;
+      DenoiseCall c;
+      memset(&c, 0, sizeof(c));
+      c.b = p->V; c.x = p->X[cur]; c.batch = 1; c.m = m; c.n = n; c.ld = n;
+      c.lam = tau * gamma; c.C = C; c.tv = tv_type; c.opts = &o; c.dual_state = p->dual;
+      c.workspace = p->fgp_ws; c.workspace_bytes = p->fgp_ws_bytes; c.stats = nullptr; c.stream = stream;
+      st = run_denoise(c);
+      if (st != CTV_OK) return st;
+      // F at the candidate, through Q's zero-padded corner
+      pr_copy<<<g, 256, 0, s>>>(p->X[cur], n, p->Q, p->N, m, n);
+      count_launch();
+      st = pr_forward_loss(p, p->Q, sqrt_y, (const float2*)H, p->loss + 1, s);
+      if (st != CTV_OK) return st;
+      pr_ls_terms<<<gr, PR_NT, 0, s>>>(p->X[cur], n, p->P, p->N, p->Gz, n, m, n, p->loss + 2);
+      count_launch();
+      double h[4];
+      if (cudaMemcpyAsync(h, p->loss, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CTV_ECUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CTV_ECUDA;
+      // F(x) <= F(z) + <x - z, grad F(z)> + ||x - z||^2 / (2 gamma)
+      if (h[1] <= h[0] + h[2] + h[3] / (2.0 * (double)gamma)) {
+        accepted = true;
+      } else {
+        gamma *= eta;
+        if (cudaMemsetAsync(p->loss + 1, 0, 3 * sizeof(double), s) != cudaSuccess) return CTV_ECUDA;
+      }
+    }
+    if (gamma_hist != nullptr) gamma_hist[k] = gamma;
+    float beta = 0.f;
+    if (accelerate) {
+      const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      beta = (float)((t - 1.0) / tn);
+      t = tn;
+    }
+    pr_fista<<<g, 256, 0, s>>>(p->X[cur], p->X[cur ^ 1], n, beta, p->P, p->N, m, n);
+    count_launch();
+    cur ^= 1;
+  }
   pr_copy<<<g, 256, 0, s>>>(p->X[cur ^ 1], n, (float2*)x_io, n, m, n);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;

@@ -256,3 +256,36 @@ def test_invalid_arguments_raise():
         ctv.denoise(b, 0.1, "tv1_iso", -1)
     with pytest.raises(RuntimeError):
         ctv.denoise(b, 0.1, "tv1_iso", 5, config=99)
+
+
+# --------------------------------------------------------------- box constraint, plain gradient projection
+@pytest.mark.parametrize("config", [0, 3, 5])
+@pytest.mark.parametrize("tv", TV_NAMES)
+def test_box_constraint(tv, config):
+    m, n = 70, 90
+    _, noisy = noisy_phantom(m, n, 0.15, seed=17)
+    box = (-0.5, 0.8, -0.3, 0.6)
+    Cg = ctv.Constraint(amp_max=None, box=box, rect=(5, 3, 60, 85))
+    Co = oracle_constraint(None, rect=(5, 3, 60, 85))
+    Co.box = box
+    x, _ = gpu_denoise(noisy, 0.06, 25, tv, 0.5, Cg, config=config)
+    b, res = run_oracle(noisy, 0.06, 25, tv, 0.5, Co)
+    check_parity(x, res, b, noisy, 0.06, tv, 0.5)
+
+
+def test_box_and_amplitude_are_exclusive():
+    b = torch.zeros(8, 8, dtype=torch.complex64, device="cuda")
+    with pytest.raises(RuntimeError):
+        ctv.denoise(b, 0.1, "tv1_iso", 5, ctv.Constraint(amp_max=1.0, box=(-1, 1, -1, 1)))
+
+
+@pytest.mark.parametrize("tv", TV_NAMES)
+def test_plain_gradient_projection(tv):
+    # Eq. (21): the same kernels with the extrapolation switched off
+    m, n = 64, 80
+    _, noisy = noisy_phantom(m, n, 0.1, seed=19)
+    Cg, Co = cons_pair("amp", m, n)
+    x, st = gpu_denoise(noisy, 0.05, 40, tv, 0.5, Cg, plain_gp=True)
+    b, res = run_oracle(noisy, 0.05, 40, tv, 0.5, Co, accelerate=False)
+    check_parity(x, res, b, noisy, 0.05, tv, 0.5)
+    assert st["iters"] == 40

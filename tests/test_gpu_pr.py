@@ -137,3 +137,44 @@ def test_full_size_first_iterations_and_convergence():
     assert np.all(np.isfinite(h))
     assert h[-1] < 0.2 * h[0]
     assert float(xg.abs().max()) <= 1 + 1e-6
+
+
+@pytest.mark.parametrize("accelerate", [True, False])
+def test_line_search_matches_oracle(accelerate):
+    # backtracking from a step that is too long: the accepted steps and the
+    # iterates agree with the oracle's FP64 line search
+    m, n, M, N = 40, 48, 80, 96
+    H, sqrt_y, x0, _ = problem(m, n, M, N, seed=13)
+    plan = ctv.PRPlan(m, n, M, N)
+    x0g, yg, Hg = to_gpu(x0, sqrt_y, H)
+    xg, hist, gam = plan.solve_ls(x0g, yg, Hg, 0.01, 8.0, 0.5, ctv.Constraint(amp_max=1.0), "tv1_aniso", 10, 8,
+                                  accelerate=accelerate)
+    torch.cuda.synchronize()
+    xo, go = opr.fista_pr_ls(x0.astype(np.complex128), sqrt_y.astype(np.float64), H.astype(np.complex128),
+                             f32(0.01), 8.0, 0.5, 8, 10, "tv1_aniso", 0.5, OC(amp_max=1.0), accelerate=accelerate)
+    assert gam == pytest.approx(go, rel=1e-6)
+    assert min(gam) < 8.0                      # the test exercised at least one backtrack
+    assert np.abs(xg.cpu().numpy() - xo.numpy()).max() <= 1e-4 * np.abs(x0).max()
+    h = hist.cpu().numpy()
+    assert np.all(np.isfinite(h))
+
+
+def test_ip_comparator_is_projected_error_reduction():
+    # tau = 0, gamma = 1, no momentum on an unpadded unitary propagator:
+    # x_{k+1} = P_C(A^*(sqrt(y) A x_k / |A x_k|))
+    from oracle.ops import P_C as oPC
+    m = n = 48
+    H, sqrt_y, x0, _ = problem(m, n, m, n, seed=21)
+    plan = ctv.PRPlan(m, n, m, n)
+    x0g, yg, Hg = to_gpu(x0, sqrt_y, H)
+    xg = ctv.api.ip_solve(plan, x0g, yg, Hg, 5, ctv.Constraint(amp_max=1.0))
+    torch.cuda.synchronize()
+    Ht = torch.tensor(H.astype(np.complex128))
+    yt = torch.tensor(sqrt_y.astype(np.float64))
+    x = torch.tensor(x0.astype(np.complex128))
+    for _ in range(5):
+        xi = opr.propagate(x, Ht)
+        v = opr.propagate_adjoint(yt * opr.unit_phase(xi), Ht)
+        u, w = oPC(v.real, v.imag, OC(amp_max=1.0))
+        x = torch.complex(u, w)
+    assert np.abs(xg.cpu().numpy() - x.numpy()).max() <= 1e-4 * np.abs(x0).max()

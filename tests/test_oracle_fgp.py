@@ -206,3 +206,23 @@ def test_warm_start_fixed_point():
     res = fgp(b, 0.05, 3000, "tv1_aniso", 0.5, C)
     res2 = fgp(b, 0.05, 5, "tv1_aniso", 0.5, C, q0=res.q)
     assert max(float((res2.x[0] - res.x[0]).abs().max()), float((res2.x[1] - res.x[1]).abs().max())) < 1e-6
+
+
+@pytest.mark.parametrize("tv_type", TV_TYPES)
+def test_certificate_box_constraint(tv_type):
+    # box on the real and imaginary parts (with a support): gap certificate and the
+    # independent primal solver agree
+    m, n = 4, 5
+    box = (-0.3, 0.6, -0.5, 0.2)
+    C = Constraint(amp_max=None, box=box, rect=(0, 1, 4, 5))
+    bz = rand_complex(m, n, 41, 0.8)
+    b = pair(bz)
+    lam, alpha = 0.1, 0.4
+    res = fgp(b, lam, 6000, tv_type, alpha, C)
+    P = float(primal_value(res.x, b, lam, tv_type, alpha))
+    D = float(dual_value(res.q, b, lam, C))
+    assert -1e-12 * P <= P - D <= 1e-9 * P
+    terms = exact.tv_terms(m, n, tv_type, alpha)
+    su, sv, best = exact.projected_subgradient(bz.real, bz.imag, lam, terms, None, C.support(m, n).numpy(),
+                                               iters=40000, box=box)
+    assert P - 1e-9 * P <= best <= P + 2e-4 * P

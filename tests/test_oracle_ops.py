@@ -165,3 +165,23 @@ def test_P_C_projection():
     z = rand_pair(3, 3, 77, scale=3.0)
     p = P_C(*z, Constraint(amp_max=0.5))
     assert float(torch.sqrt(p[0] ** 2 + p[1] ** 2).max()) <= 0.5 + 1e-15
+
+
+def test_P_C_box():
+    # the box of the real and imaginary parts: componentwise clamps, in the set,
+    # idempotent and satisfying the variational inequality
+    m, n = 5, 6
+    box = (-0.4, 0.7, -0.2, 0.5)
+    C = Constraint(amp_max=None, box=box)
+    for seed in range(3):
+        z = rand_pair(m, n, 60 + seed, scale=1.2)
+        p = P_C(*z, C)
+        assert float(p[0].min()) >= box[0] and float(p[0].max()) <= box[1]
+        assert float(p[1].min()) >= box[2] and float(p[1].max()) <= box[3]
+        pp = P_C(*p, C)
+        assert torch.equal(pp[0], p[0]) and torch.equal(pp[1], p[1])
+        for s2 in range(4):
+            y = rand_pair(m, n, 700 + s2)
+            y = (torch.clamp(y[0], box[0], box[1]), torch.clamp(y[1], box[2], box[3]))
+            vi = pair_inner((z[0] - p[0], z[1] - p[1]), (y[0] - p[0], y[1] - p[1]))
+            assert float(vi) <= 1e-12

@@ -122,3 +122,27 @@ def test_fista_one_step_is_prox_of_gradient_step():
     v = x0 - gamma * pr.fidelity_grad(x0, sqrt_y, H)
     res = fgp((v.real.clone(), v.imag.clone()), tau * gamma, 7, "tv2_iso", 0.5, C)
     assert float((x1 - torch.complex(*res.x)).abs().max()) == 0.0
+
+
+def test_line_search_reduces_to_fixed_step_and_backtracks():
+    H, sqrt_y, x0, _ = _pr_problem(24, 7)
+    C = Constraint(amp_max=1.0)
+    # a step that always passes the sufficient-decrease test: identical to the fixed-step run
+    x_ls, gam = pr.fista_pr_ls(x0, sqrt_y, H, 0.01, 0.25, 0.5, 6, 5, "tv1_aniso", 0.5, C)
+    assert gam == [0.25] * 6
+    x_fx, _ = pr.fista_pr(x0, sqrt_y, H, 0.01, 0.25, 6, 5, "tv1_aniso", 0.5, C)
+    assert float((x_ls - x_fx).abs().max()) == 0.0
+    # a step that is far too long is shortened, never lengthened, and each accepted
+    # step satisfies the sufficient-decrease inequality at the iterate it was taken from
+    x_ls, gam = pr.fista_pr_ls(x0, sqrt_y, H, 0.01, 64.0, 0.5, 6, 5, "tv1_aniso", 0.5, C, accelerate=False)
+    assert gam[0] < 64.0 and all(a >= b for a, b in zip(gam, gam[1:]))
+    z = torch.as_tensor(x0).to(torch.complex128)
+    from oracle.fgp import fgp as _fgp
+    g = pr.fidelity_grad(z, sqrt_y, H)
+    v = z - gam[0] * g
+    res = _fgp((v.real.clone(), v.imag.clone()), 0.01 * gam[0], 5, "tv1_aniso", 0.5, C)
+    x1 = torch.complex(*res.x)
+    d = x1 - z
+    rhs = pr.fidelity(z, sqrt_y, H) + float((d.real * g.real + d.imag * g.imag).sum()) + \
+        float((d.abs() ** 2).sum()) / (2 * gam[0])
+    assert pr.fidelity(x1, sqrt_y, H) <= rhs
