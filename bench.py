@@ -180,7 +180,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--workload", default="denoise2048",
-                    choices=("denoise2048", "denoise256", "batched", "pr", "backward"),
+                    choices=("denoise2048", "denoise256", "batched", "pr", "backward", "pr_paper"),
                     help="denoise2048 is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -467,6 +467,39 @@ def run_other_workload(args, world, rank, local):
                     "loss_first": float(h[0]), "loss_last": float(h[-1]),
                     "phase_rmse_initial": float(np.sqrt((ph0 ** 2).mean())),
                     "phase_rmse_final": float(np.sqrt((ph ** 2).mean()))})
+    elif args.workload == "pr_paper":
+        # the paper's simulated setting (Sec. VI-A): 256^2 pure phase object (phase in [0, pi]),
+        # angular spectrum at 500 nm, 5 um pixels, 5 mm, 10% Gaussian intensity noise, back-propagated
+        # start, type-I anisotropic TV, 10 FGP iterations per outer iteration; IP vs TV (C = C^n) vs CTV
+        from phantoms import angular_spectrum_tf, intensity_with_gaussian_noise, phase_object, phase_rmse
+        m = n = 256
+        H = angular_spectrum_tf(m, n, 500e-9, 5e-6, 5e-3).astype(np.complex64)
+        x_gt = phase_object(m, n, seed=31)
+        y = intensity_with_gaussian_noise(x_gt, H.astype(np.complex128), 0.1, seed=32)
+        sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
+        Hg = torch.from_numpy(H).to(dev)
+        plan = ctv.PRPlan(m, n, m, n)
+        g0, _ = plan.gradient(torch.zeros(m, n, dtype=torch.complex64, device=dev), sqrt_y, Hg)
+        x0 = (-g0).contiguous()
+        tau = 0.005
+        curves = {}
+        t0 = time.perf_counter()
+        for name in ("IP", "TV", "CTV"):
+            rm = []
+            for K in range(10, 151, 10):      # the state after K outer iterations, from x_0 each time
+                if name == "IP":
+                    x = ctv.api.ip_solve(plan, x0, sqrt_y, Hg, K, ctv.Constraint(amp_max=1.0))
+                else:
+                    C = ctv.Constraint(amp_max=1.0) if name == "CTV" else ctv.NO_CONSTRAINT
+                    x = plan.solve(x0, sqrt_y, Hg, tau, 1.0, C, "tv1_aniso", 10, K)
+                rm.append(phase_rmse(x.cpu().numpy(), x_gt))
+            curves[name] = rm
+        dt = time.perf_counter() - t0
+        out.update({"metric": "phase RMSE (rad) after 50/100/150 outer iterations, paper's simulated setting",
+                    "value": curves["CTV"][-1], "unit": "rad", "higher_is_better": False,
+                    "rmse_initial": phase_rmse(x0.cpu().numpy(), x_gt),
+                    "rmse_at_50_100_150": {k: [v[4], v[9], v[14]] for k, v in curves.items()},
+                    "curves_every_10": curves, "tau": tau, "wall_s": dt})
     elif args.workload == "backward":
         # 8 x 1024^2, 50 unrolled iterations, checkpoints every 10, loss ||x - x_gt||^2
         Bn, m, n, K = 8, 1024, 1024, 50

@@ -5,9 +5,6 @@
 //   kind 0  fgp_tile:       region A x B pixels (RW x RH), C threads, T iterations per launch
 //   kind 1  fgp_strip_tile: A warps across, B warps down, C pixels per thread
 //                           (region 32A x BC pixels, 32AB threads)
-//   kind 2  as kind 1, but a single-image solve without gap checks runs all its
-//           passes in one cooperative launch (persistent.cu) when every tile can
-//           have its own resident block; otherwise it runs as kind 1
 #pragma once
 
 #include "ctv_device.cuh"
@@ -27,9 +24,7 @@
   X(11, 1, 4, 2, 8, 4)       \
   X(12, 1, 2, 2, 8, 4)       \
   X(13, 1, 4, 2, 16, 4)      \
-  X(14, 1, 6, 2, 16, 4)      \
-  X(15, 2, 4, 1, 4, 8)       \
-  X(16, 2, 4, 2, 8, 4)
+  X(14, 1, 6, 2, 16, 4)
 
 namespace ctv {
 

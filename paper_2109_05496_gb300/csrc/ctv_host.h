@@ -40,9 +40,6 @@ int size_class(int m, int n);
 int num_configs();
 bool config_info(int i, int* T, int* RW, int* RH, int* NT);
 
-struct PassParams;
-bool is_persistent_config(int cfg);
-
 // Measurement hooks (prof.cu): count every launch; time fused passes when enabled.
 void count_launch();
 int prof_begin(cudaStream_t s);

@@ -69,9 +69,5 @@ inline int cons_mode(const ConsDev& c) {
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s);
 // Grid of the fused pass for configuration cfg over an m x n image batch.
 dim3 pass_grid(int cfg, int m, int n, int batch);
-// All passes of one image in one cooperative launch (persistent.cu); returns
-// CTV_EUNSUPPORTED without launching when the tiles cannot all be resident.
-ctv_status run_persistent(int cfg, int tv, const PassParams& p, int K, bool warm, const float4* dual_q,
-                          unsigned int* bar, int* status, int* last_set, cudaStream_t s);
 
 }  // namespace ctv

@@ -246,28 +246,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
     p.st = st;
     const dim3 grid = pass_grid(cfg, c.m, c.n, c.batch);
     if (grid.y > 65535) return CTV_EINVAL;
-    bool done = false;
-    if (is_persistent_config(cfg) && check_every == 0 && c.batch == 1 && c.lam_dev == nullptr) {
-      p.q_in = set_q[0];
-      p.r_in = set_r[0];
-      p.q_out = set_q[1];
-      p.r_out = set_r[1];
-      int ls = 0;
-      const int slot = prof_begin(s);
-      const ctv_status ps = run_persistent(cfg, c.tv, p, K, warm != 0, (const float4*)c.dual_state,
-                                           (unsigned int*)&st->acc[3], &st->status, &ls, s);
-      if (ps == CTV_OK) {
-        count_launch();
-        prof_end(slot, s, (double)px * (double)K);
-        last_set = ls;
-        done = true;
-      } else if (ps != CTV_EUNSUPPORTED) {
-        return ps;
-      } else {
-        prof_end(slot, s, 0.0);
-      }
-    }
-    int k = done ? K + 1 : 1;
+    int k = 1;
     int out = 0;
     const float4* q_in = (const float4*)c.dual_state;
     const float4* r_in = (const float4*)c.dual_state;

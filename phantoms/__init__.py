@@ -139,3 +139,29 @@ def simulate_intensity(x: np.ndarray, H: np.ndarray, seed: int, photons: float =
         rng = np.random.default_rng(seed)
         y = rng.poisson(photons * y) / photons
     return y
+
+
+def phase_object(m: int, n: int, seed: int) -> np.ndarray:
+    """Pure phase object exp(i phi) with a piecewise-constant phi in [0, pi]
+    (the phase of a phantom, rescaled), standing in for the test images of the
+    paper's simulated phase-retrieval experiments."""
+    ph = np.angle(phantom(m, n, seed))
+    ph = math.pi * (ph - ph.min()) / max(ph.max() - ph.min(), 1e-12)
+    return np.exp(1j * ph)
+
+
+def intensity_with_gaussian_noise(x: np.ndarray, H: np.ndarray, level: float, seed: int) -> np.ndarray:
+    """y = |A x|^2 + n, n ~ N(0, (level * mean |A x|^2)^2), clipped at 0 (the
+    "10% Gaussian noise added to the calculated intensity" of Sec. VI-A, read as
+    a standard deviation of level times the mean intensity)."""
+    y = simulate_intensity(x, H, seed, photons=0)
+    rng = np.random.default_rng(seed)
+    return np.maximum(y + rng.normal(0.0, level * float(y.mean()), y.shape), 0.0)
+
+
+def phase_rmse(x: np.ndarray, x_true: np.ndarray) -> float:
+    """RMSE of the phase of x against x_true with the global phase offset removed
+    (the error measure of Sec. VI-A)."""
+    d = np.angle(x * np.conj(x_true))
+    d = np.angle(np.exp(1j * (d - np.angle(np.exp(1j * d).mean()))))
+    return float(np.sqrt((d ** 2).mean()))

@@ -289,30 +289,3 @@ def test_plain_gradient_projection(tv):
     b, res = run_oracle(noisy, 0.05, 40, tv, 0.5, Co, accelerate=False)
     check_parity(x, res, b, noisy, 0.05, tv, 0.5)
     assert st["iters"] == 40
-
-
-# --------------------------------------------------------------- single-launch (persistent) solves
-@pytest.mark.parametrize("pair", [(15, 9), (16, 11)])
-@pytest.mark.parametrize("shape", [(256, 256), (100, 37), (1, 1), (300, 200)])
-@pytest.mark.parametrize("tv", TV_NAMES)
-def test_persistent_matches_pass_per_launch(pair, shape, tv):
-    # the cooperative single-launch solve runs the same tiles as the per-launch
-    # configuration with the same geometry: identical bits, and the oracle agrees
-    m, n = shape
-    _, noisy = noisy_phantom(m, n, 0.1, seed=m + n)
-    Cg, Co = cons_pair("amp_rect", m, n)
-    b = torch.from_numpy(to_c64(noisy)).cuda()
-    dual1 = torch.zeros(m * n * 4, dtype=torch.float32, device="cuda")
-    dual2 = torch.zeros_like(dual1)
-    x1, s1 = ctv.denoise(b, 0.05, tv, 37, Cg, 0.5, config=pair[0], dual_state=dual1, return_stats=True)
-    x2, s2 = ctv.denoise(b, 0.05, tv, 37, Cg, 0.5, config=pair[1], dual_state=dual2, return_stats=True)
-    torch.cuda.synchronize()
-    assert torch.equal(x1, x2) and torch.equal(dual1, dual2)
-    assert s1["status"] == 0 and s1["iters"] == 37 and s1["primal"] == s2["primal"]
-    bp, res = run_oracle(noisy, 0.05, 37, tv, 0.5, Co)
-    check_parity(x1.cpu().numpy(), res, bp, noisy, 0.05, tv, 0.5)
-    # warm start through the single launch as well
-    x3 = ctv.denoise(b, 0.05, tv, 9, Cg, 0.5, config=pair[0], dual_state=dual1, warm_start=True)
-    x4 = ctv.denoise(b, 0.05, tv, 9, Cg, 0.5, config=pair[1], dual_state=dual2, warm_start=True)
-    torch.cuda.synchronize()
-    assert torch.equal(x3, x4)
