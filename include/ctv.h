@@ -201,7 +201,8 @@ int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lamb
  * Batched denoising of many images of uneven sizes (problem (1) per image).
  * Each image has its own shape, lambda, alpha, TV type and C; all share
  * opts->max_iters, check_every and gap_tol (warm_start must be 0; config -1
- * picks one). ctv_plan_create copies the descriptors, allocates the plan's
+ * picks one; plans support configurations 2, 7, 11 and 14, others return
+ * CTV_EUNSUPPORTED). ctv_plan_create copies the descriptors, allocates the plan's
  * device memory (dual state 64 bytes per pixel plus work lists) and captures the
  * whole schedule - one launch per pass over the tiles of all images - into a
  * CUDA graph; ctv_plan_execute replays it on `stream` (asynchronous). The b and

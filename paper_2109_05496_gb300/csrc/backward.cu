@@ -18,7 +18,9 @@
 // Each segment of ckpt_every iterations is first recomputed from its
 // checkpoint by the fused pass, storing every r_k of the segment, then walked
 // backwards one reverse step per launch (adj_strip_kernel: a two-pixel halo,
-// since the reverse step reads two stencils deep). All Jacobians are those of the projections, which
+// since the reverse step reads two stencils deep). (Running the next segment's
+// recompute on a second stream during the walk back was measured: both kernels
+// fill the GPU, so it saved nothing.) All Jacobians are those of the projections, which
 // are symmetric; at a projection's boundary the interior branch (identity) is
 // taken, and the projection onto a radius-0 ball has Jacobian 0.
 #include <cuda_runtime.h>
@@ -57,6 +59,26 @@ __device__ __forceinline__ float2 proj_C_adj(float2 w, float2 xb, int gj, int gk
     if (w.y < c.im_lo || w.y > c.im_hi) xb.y = 0.f;
   }
   return xb;
+}
+
+// proj_C_adj specialised like proj_C_t (kin: the pixel's column is inside the rectangle)
+template <int CONS>
+__device__ __forceinline__ float2 proj_C_adj_t(float2 w, float2 xb, int gj, int gk, bool kin, const ConsDev& c) {
+  if (CONS == CONS_NONE) return xb;
+  if (CONS == CONS_RECT && (!kin || gj < c.j0 || gj >= c.j1)) return make_float2(0.f, 0.f);
+  if (CONS == CONS_AMP || (CONS == CONS_RECT && c.amp)) {
+    const float a2 = w.x * w.x + w.y * w.y;
+    if (a2 > c.amax * c.amax) {
+      const float inv = rsqrtf(a2);
+      const float nx = w.x * inv, ny = w.y * inv;
+      const float dot = nx * xb.x + ny * xb.y;
+      const float s = c.amax * inv;
+      return make_float2(s * (xb.x - nx * dot), s * (xb.y - ny * dot));
+    }
+    return xb;
+  }
+  if (CONS == CONS_RECT) return xb;
+  return proj_C_adj(w, xb, gj, gk, c);
 }
 
 // (a, b) <- J^T (a, b) for the projection of the pair (u, v) onto the ball of radius rad
@@ -223,7 +245,10 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
 // configurations available to the recompute (a subset of the pass table)
 #define CTV_HIST_CONFIGS(X) \
   X(2, 0, 4, 64, 32, 256)   \
-  X(5, 1, 6, 2, 8, 8)
+  X(3, 1, 4, 2, 4, 8)       \
+  X(5, 1, 6, 2, 8, 8)       \
+  X(11, 1, 4, 2, 8, 4)      \
+  X(14, 1, 6, 2, 16, 4)
 
 template <int KIND, int TV, int T, int A, int B, int C>
 static cudaError_t launch_hist_t(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
@@ -273,14 +298,12 @@ static bool hist_config_ok(int cfg) {
 // a warp covers 32 columns, each thread PPT consecutive rows of its column, so
 // the vertical neighbours of the four stencil phases come from registers except
 // at strip ends. Region 32 WX x PPT WY with a two-pixel halo.
-template <int TV, int WX, int WY, int PPT, int CONS>
-__global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
+template <int TV, int WX, int WY, int PPT, int CONS, bool EDGE>
+__device__ __forceinline__ void adj_strip_body(const AdjParams& p, float2* smf2, double* red) {
   constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH, NT = 32 * WX * WY;
-  extern __shared__ float2 smf2[];
   float2* S2 = smf2;          // p2 of r (phase A), then p2 of ebar (phases B-C)
   float2* XW = S2 + R;        // x (A-B), then what (C-D)
   float2* B1 = XW + R;        // strip-bottom p1 of r (A), then of ebar (B-C)
-  __shared__ double red[NT / 32];
   const int z = blockIdx.z;
   const long long off = (long long)z * p.px;
   const float lam = fmaxf(p.lam_dev[z], 0.f);
@@ -291,10 +314,10 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
   const int lk = wx * 32 + lane, lj0 = wy * PPT;
   const int gk = blockIdx.x * (RW - 4) - 2 + lk;
   const int gj0 = blockIdx.y * (RH - 4) - 2 + lj0;
-  const bool colin = (unsigned)gk < (unsigned)n;
+  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
   const bool kin = gk >= p.C.k0 && gk < p.C.k1;
   const bool kint = lk >= 2 && lk < RW - 2;
-  const bool right_in = lk < RW - 1 && gk < n - 1;
+  const bool right_in = lk < RW - 1 && (!EDGE || gk < n - 1);
   const bool strip_next = lj0 + PPT < RH;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
@@ -307,7 +330,7 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
     qb[s] = z4;
     bb[s] = z2;
     ba[s] = z2;
-    if (colin && (unsigned)gj < (unsigned)m) {
+    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
       const long long o = off + (long long)gj * n + gk;
       if (p.r != nullptr) r[s] = __ldg(p.r + o);
       bb[s] = __ldg(p.b + o);
@@ -334,7 +357,7 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
     dd[s] = z2;
     ww[s] = z2;
     xx[s] = z2;
-    if (colin && (unsigned)gj < (unsigned)m) {
+    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
       float2 up;
       if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
       else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
@@ -354,9 +377,9 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
     gb[s] = z4;
     e1[s] = z2;
     e2[s] = z2;
-    if (colin && (unsigned)gj < (unsigned)m) {
+    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
       float ea = 0.f, eb_ = 0.f, ec = 0.f, ed = 0.f;
-      if (gj < m - 1) {
+      if (!EDGE || gj < m - 1) {
         float2 xd;
         if (s < PPT - 1) xd = xx[s + 1];
         else xd = strip_next ? XW[(lj0 + s + 1) * RW + lk] : xx[s];
@@ -370,8 +393,8 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
       }
       const float4 g = f4(r[s].x + c8 * ea, r[s].y + c8 * eb_, r[s].z + c8 * ec, r[s].w + c8 * ed);
       float4 gbar = proj_S_adj<TV>(g, qb[s], p.alpha);
-      if (gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
-      if (gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
+      if (EDGE && gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
+      if (EDGE && gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
       gb[s] = gbar;
       e1[s] = make_float2(c8 * gbar.x, c8 * gbar.y);
       e2[s] = make_float2(c8 * gbar.z, c8 * gbar.w);
@@ -389,13 +412,13 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
   for (int s = 0; s < PPT; ++s) {
     const int gj = gj0 + s;
     float2 wh = z2;
-    if (colin && (unsigned)gj < (unsigned)m) {
+    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
       float2 up;
       if (s > 0) up = e1[s - 1];
       else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
       const float2 left = lk > 0 ? S2[(lj0 + s) * RW + lk - 1] : z2;
       const float2 xb = make_float2(e1[s].x - up.x + e2[s].x - left.x, e1[s].y - up.y + e2[s].y - left.y);
-      wh = proj_C_adj(ww[s], xb, gj, gk, p.C);
+      wh = proj_C_adj_t<CONS>(ww[s], xb, gj, gk, kin, p.C);
       const int lj = lj0 + s;
       if (kint && lj >= 2 && lj < RH - 2) {
         p.bbar[off + (long long)gj * n + gk] = make_float2(ba[s].x + wh.x, ba[s].y + wh.y);
@@ -411,14 +434,14 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int lj = lj0 + s, gj = gj0 + s;
-      if (lj >= 2 && lj < RH - 2 && (unsigned)gj < (unsigned)m) {
+      if (lj >= 2 && lj < RH - 2 && (!EDGE || (unsigned)gj < (unsigned)m)) {
         float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-        if (gj < m - 1) {
+        if (!EDGE || gj < m - 1) {
           const float2 wd = s < PPT - 1 ? xx[s + 1] : XW[(lj0 + s + 1) * RW + lk];
           d1r = xx[s].x - wd.x;
           d1i = xx[s].y - wd.y;
         }
-        if (gk < n - 1) {
+        if (!EDGE || gk < n - 1) {
           const float2 wr = XW[(lj0 + s) * RW + lk + 1];
           d2r = xx[s].x - wr.x;
           d2i = xx[s].y - wr.y;
@@ -433,14 +456,30 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
   if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
 }
 
+template <int TV, int WX, int WY, int PPT, int CONS>
+__global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
+  constexpr int RW = 32 * WX, RH = PPT * WY;
+  extern __shared__ float2 smf2[];
+  __shared__ double red[WX * WY];
+  const int gj0 = blockIdx.y * (RH - 4) - 2, gk0 = blockIdx.x * (RW - 4) - 2;
+  // fast path for regions inside the image away from its last row and column
+  const bool inside = gj0 >= 0 && gk0 >= 0 && gj0 + RH <= p.m - 1 && gk0 + RW <= p.n - 1;
+  if (inside) adj_strip_body<TV, WX, WY, PPT, CONS, false>(p, smf2, red);
+  else adj_strip_body<TV, WX, WY, PPT, CONS, true>(p, smf2, red);
+}
+
 // reverse-step geometry: warps across, warps down, rows per thread
 #ifndef CTV_ADJ_CFG
-#define CTV_ADJ_CFG 3
+#define CTV_ADJ_CFG 4
 #endif
 #if CTV_ADJ_CFG == 1
 constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 4;    // 64 x 32 region, 512 threads
 #elif CTV_ADJ_CFG == 2
 constexpr int AS_WX = 2, AS_WY = 4, AS_PPT = 4;    // 64 x 16 region, 256 threads
+#elif CTV_ADJ_CFG == 4
+constexpr int AS_WX = 1, AS_WY = 8, AS_PPT = 2;    // 32 x 16 region, 256 threads
+#elif CTV_ADJ_CFG == 5
+constexpr int AS_WX = 1, AS_WY = 16, AS_PPT = 2;   // 32 x 32 region, 512 threads
 #else
 constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 2;    // 64 x 16 region, 512 threads
 #endif
@@ -498,7 +537,7 @@ struct UnrolledLayout {
   float4* finr;
   float4* setq[2];
   float4* setr[2];
-  float4* hist;                    // ckpt planes
+  float4* hist;                    // ckpt planes: r_k of the segment being walked back
   float4* rb[3];
   size_t bytes;
 };
@@ -701,32 +740,31 @@ int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* la
   PassParams p = base_pass(a, cons);
   const dim3 grid = pass_grid(cfg, m, n, batch);
   const int nseg = (K + c - 1) / c;
+  // each segment: recompute it from its checkpoint (storing every r_k), then walk it back
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * c, k1 = std::min(k0 + c, K);
     // recompute iterations k0+1 .. k1-1, keeping r_{k0+2} .. r_{k1}
-    if (k1 - k0 - 1 > 0) {
-      const float4* qin = sg == 0 ? nullptr : L.ckq[(size_t)sg];
-      const float4* rin = sg == 0 ? nullptr : L.ckr[(size_t)sg];
-      bool first = sg == 0;
-      int kk = k0 + 1, out = 0;
-      while (kk <= k1 - 1) {
-        const int steps = std::min(T, k1 - 1 - kk + 1);
-        for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)kk + i] : 0.f;
-        p.nsteps = steps;
-        p.first = first ? 1 : 0;
-        p.q_in = qin;
-        p.r_in = rin;
-        p.q_out = L.setq[out];
-        p.r_out = L.setr[out];
-        if (launch_hist(tv_type, cfg, p, grid, L.hist + (long long)(kk - k0 - 1) * plane, plane, s) != cudaSuccess)
-          return CTV_ECUDA;
-        count_launch();
-        qin = L.setq[out];
-        rin = L.setr[out];
-        out ^= 1;
-        first = false;
-        kk += steps;
-      }
+    const float4* qin = sg == 0 ? nullptr : L.ckq[(size_t)sg];
+    const float4* rin = sg == 0 ? nullptr : L.ckr[(size_t)sg];
+    bool first = sg == 0;
+    int kk = k0 + 1, out = 0;
+    while (kk <= k1 - 1) {
+      const int steps = std::min(T, k1 - 1 - kk + 1);
+      for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)kk + i] : 0.f;
+      p.nsteps = steps;
+      p.first = first ? 1 : 0;
+      p.q_in = qin;
+      p.r_in = rin;
+      p.q_out = L.setq[out];
+      p.r_out = L.setr[out];
+      if (launch_hist(tv_type, cfg, p, grid, L.hist + (long long)(kk - k0 - 1) * plane, plane, s) != cudaSuccess)
+        return CTV_ECUDA;
+      count_launch();
+      qin = L.setq[out];
+      rin = L.setr[out];
+      out ^= 1;
+      first = false;
+      kk += steps;
     }
     for (int k = k1; k >= k0 + 1; --k) {
       const float4* rk;

@@ -100,6 +100,7 @@ dim3 pass_grid(int cfg, int m, int n, int batch) {
 }
 
 int default_config(int m, int n, int iters, int tv) {
+  if (m <= 0 || n <= 0) return 11;   // plans of many images (see plan.cu for the configurations they support)
   if (iters < 2) return 0;
   if (m > 0 && n > 0) {
     const int t = tuned_config(m, n, tv);

@@ -3,9 +3,9 @@
 // A plan holds, in one device allocation, a descriptor per image (its own m, n,
 // lambda, alpha, TV type, C and dual buffers) and two work lists of tiles over
 // all images: one for the fused FGP pass, one for the gap / finalize
-// evaluation. Each pass of Algorithm 2 is then a single launch whose blocks each
-// take one tile of one image (the TV type is chosen per block), so small images
-// no longer pay a launch each. The whole schedule (zeroing of the per-image
+// evaluation. Each pass of Algorithm 2 is then one launch per TV type present,
+// whose blocks each take one tile of one image of that type, so small images no
+// longer pay a launch each and each launch keeps the register budget of its type. The whole schedule (zeroing of the per-image
 // records, the passes, the optional gap checks and the finalize) is captured
 // once into a CUDA graph on a private stream and replayed on the caller's stream
 // by ctv_plan_execute. Every image keeps its own stopping test.
@@ -21,6 +21,7 @@
 #include "ctv_device.cuh"
 #include "gap_device.cuh"
 #include "ctv_host.h"
+#include "ctv_kernels.h"
 
 namespace ctv {
 
@@ -55,7 +56,7 @@ struct ListPassParams {
   float beta[8];
 };
 
-template <int KIND, int T, int A, int B, int C>
+template <int KIND, int TV, int CONS, int T, int A, int B, int C>
 __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kernel(ListPassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
   const WorkItem w = p.items[blockIdx.x];
@@ -73,14 +74,10 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kern
   I.lam = d.lam;
   I.alpha = d.alpha;
   I.C = d.C;
+  I.r_hist = nullptr;
+  I.hist_plane = 0;
   const int j0 = (w.tile / d.tiles_x) * (G::RH - 2 * T), k0 = (w.tile % d.tiles_x) * (G::RW - 2 * T);
-  const bool first = p.first != 0;
-  switch (d.tv) {
-    case TV1_ISO: run_tile<KIND, TV1_ISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
-    case TV1_ANISO: run_tile<KIND, TV1_ANISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
-    case TV2_ISO: run_tile<KIND, TV2_ISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
-    default: run_tile<KIND, TV2_ANISO, T, A, B, C>(I, j0, k0, p.beta, p.nsteps, first); break;
-  }
+  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, j0, k0, p.beta, p.nsteps, p.first != 0);
 }
 
 struct ListGapParams {
@@ -125,25 +122,67 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
   gap_commit(d.st, acc, d.gnblk, d.lam, false, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
 }
 
-template <int KIND, int T, int A, int B, int C>
+template <int KIND, int TV, int CONS, int T, int A, int B, int C>
 static cudaError_t launch_list_t(const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
   using G = CfgGeom<KIND, A, B, C>;
   if (set_attr) {
-    return cudaFuncSetAttribute(fgp_pass_list_kernel<KIND, T, A, B, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)G::SMEM);
+    return cudaFuncSetAttribute(fgp_pass_list_kernel<KIND, TV, CONS, T, A, B, C>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   }
-  fgp_pass_list_kernel<KIND, T, A, B, C><<<nblocks, G::NT, G::SMEM, s>>>(p);
+  fgp_pass_list_kernel<KIND, TV, CONS, T, A, B, C><<<nblocks, G::NT, G::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_list(int cfg, const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
+template <int KIND, int TV, int T, int A, int B, int C>
+static cudaError_t launch_list_cons(int cons, const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
+  if constexpr (KIND == 0) {
+    return launch_list_t<KIND, TV, CONS_GEN, T, A, B, C>(p, nblocks, s, set_attr);
+  } else {
+    switch (cons) {
+      case CONS_NONE: return launch_list_t<KIND, TV, CONS_NONE, T, A, B, C>(p, nblocks, s, set_attr);
+      case CONS_AMP: return launch_list_t<KIND, TV, CONS_AMP, T, A, B, C>(p, nblocks, s, set_attr);
+      case CONS_RECT: return launch_list_t<KIND, TV, CONS_RECT, T, A, B, C>(p, nblocks, s, set_attr);
+      default: return launch_list_t<KIND, TV, CONS_GEN, T, A, B, C>(p, nblocks, s, set_attr);
+    }
+  }
+}
+
+// configurations a plan can use (a subset of the pass table, to bound build time)
+#define CTV_PLAN_CONFIGS(X)   \
+  X(2, 0, 4, 64, 32, 256)     \
+  X(7, 1, 3, 2, 8, 4)         \
+  X(11, 1, 4, 2, 8, 4)        \
+  X(14, 1, 6, 2, 16, 4)
+
+static bool plan_config_ok(int cfg) {
+#define CTV_PLAN_ID(id, kind, T, A, B, C) if (cfg == id) return true;
+  CTV_PLAN_CONFIGS(CTV_PLAN_ID)
+#undef CTV_PLAN_ID
+  return false;
+}
+
+template <int TV>
+static cudaError_t launch_list_tv(int cfg, int cons, const ListPassParams& p, int nblocks, cudaStream_t s,
+                                  bool set_attr) {
   switch (cfg) {
 #define CTV_CFG_CASE(id, kind, T, A, B, C) \
-  case id: return launch_list_t<kind, T, A, B, C>(p, nblocks, s, set_attr);
-    CTV_PASS_CONFIGS(CTV_CFG_CASE)
+  case id: return launch_list_cons<kind, TV, T, A, B, C>(cons, p, nblocks, s, set_attr);
+    CTV_PLAN_CONFIGS(CTV_CFG_CASE)
 #undef CTV_CFG_CASE
   }
   return cudaErrorInvalidValue;
+}
+
+// One launch over the work items of the images of one TV type (items sorted by
+// type), so that every launch uses the register budget of that type alone.
+static cudaError_t launch_list(int tv, int cfg, int cons, const ListPassParams& p, int nblocks, cudaStream_t s,
+                               bool set_attr) {
+  switch (tv) {
+    case TV1_ISO: return launch_list_tv<TV1_ISO>(cfg, cons, p, nblocks, s, set_attr);
+    case TV1_ANISO: return launch_list_tv<TV1_ANISO>(cfg, cons, p, nblocks, s, set_attr);
+    case TV2_ISO: return launch_list_tv<TV2_ISO>(cfg, cons, p, nblocks, s, set_attr);
+    default: return launch_list_tv<TV2_ANISO>(cfg, cons, p, nblocks, s, set_attr);
+  }
 }
 
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -160,6 +199,8 @@ struct ctv_plan {
   ctv::PlanImg* d_imgs;
   ctv::WorkItem* d_pass;
   int n_pass;
+  int tv_begin[5];   // pass items of TV type t are [tv_begin[t], tv_begin[t + 1])
+  int cons;          // constraint specialisation shared by every image (CONS_GEN if they differ)
   ctv::WorkItem* d_gap;
   int n_gap;
   ctv::DevStats* d_st;
@@ -200,8 +241,13 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
       p.first = first ? 1 : 0;
       p.in_set = out ^ 1;
       p.out_set = out;
-      if (launch_list(P->cfg, p, P->n_pass, s, false) != cudaSuccess) return CTV_ECUDA;
-      ++launches;
+      for (int t = 0; t < 4; ++t) {
+        const int nb = P->tv_begin[t + 1] - P->tv_begin[t];
+        if (nb == 0) continue;
+        p.items = P->d_pass + P->tv_begin[t];
+        if (launch_list(t, P->cfg, P->cons, p, nb, s, false) != cudaSuccess) return CTV_ECUDA;
+        ++launches;
+      }
       first = false;
       k += steps;
       last_set = out;
@@ -242,6 +288,7 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   int cfg = opts->config;
   if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
   if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1);
+  if (!plan_config_ok(cfg)) return CTV_EUNSUPPORTED;
   int T = 1, RW = 0, RH = 0, NT = 0;
   config_info(cfg, &T, &RW, &RH, &NT);
   const int TW = RW - 2 * T, TH = RH - 2 * T;
@@ -279,6 +326,14 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
     px_total += (double)d.m * d.n;
   }
   if (pass_items.size() > 0x7fffffffu || gap_items.size() > 0x7fffffffu) return CTV_EINVAL;
+  std::stable_sort(pass_items.begin(), pass_items.end(),
+                   [&](const WorkItem& a, const WorkItem& b) { return imgs[(size_t)a.img].tv < imgs[(size_t)b.img].tv; });
+  int tv_begin[5] = {0, 0, 0, 0, 0};
+  for (const WorkItem& w : pass_items) tv_begin[imgs[(size_t)w.img].tv + 1]++;
+  for (int t = 0; t < 4; ++t) tv_begin[t + 1] += tv_begin[t];
+  int cons = cons_mode(imgs[0].C);
+  for (int i = 1; i < count; ++i)
+    if (cons_mode(imgs[(size_t)i].C) != cons) cons = CONS_GEN;
 
   ctv_plan* P = new ctv_plan();
   P->count = count;
@@ -287,6 +342,8 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   P->gap_tol = opts->gap_tol;
   P->cfg = cfg;
   P->n_pass = (int)pass_items.size();
+  for (int t = 0; t < 5; ++t) P->tv_begin[t] = tv_begin[t];
+  P->cons = cons;
   P->n_gap = (int)gap_items.size();
   P->pixel_iters = px_total * P->K;
   nesterov_betas(P->K, &P->beta);
@@ -318,7 +375,7 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
             cudaMemcpy(P->d_gap, gap_items.data(), sizeof(WorkItem) * gap_items.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ListPassParams dummy;
   memset(&dummy, 0, sizeof(dummy));
-  ok = ok && launch_list(cfg, dummy, 0, nullptr, true) == cudaSuccess;
+  for (int t = 0; t < 4; ++t) ok = ok && launch_list(t, cfg, cons, dummy, 0, nullptr, true) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     cudaFree(P->dev);

@@ -59,3 +59,33 @@ def test_null_arguments_rejected_before_any_launch(lib):
     opts = _lib.CtvOpts(10, 0, 0.0, 0.5, 0, -1)
     st = lib.ctv_denoise(None, None, 8, 8, 8, 0.1, None, 0, opts, None, None, 0, None, None)
     assert st == 1
+
+
+def test_tune_table_host_only(lib):
+    import ctypes
+    assert lib.ctv_size_class(1024, 1024) == 20
+    assert lib.ctv_size_class(0, 5) == -1
+    v = ctypes.c_int()
+    assert lib.ctv_tune_get(20, 1, ctypes.byref(v)) == 0
+    before = v.value
+    assert lib.ctv_tune_set(20, 1, 3) == 0
+    assert lib.ctv_tune_get(20, 1, ctypes.byref(v)) == 0 and v.value == 3
+    assert lib.ctv_default_config(1024, 1024, 100, 1) == 3      # the tuned choice wins
+    assert lib.ctv_tune_set(20, 1, before) == 0
+    assert lib.ctv_tune_set(20, 9, 3) == 1 and lib.ctv_tune_set(99, 0, 3) == 1   # CTV_EINVAL
+    assert lib.ctv_tune_set(20, 1, lib.ctv_num_configs()) == 1
+    assert lib.ctv_default_config(2048, 2048, 1, 0) == 0        # a single iteration needs no blocking
+
+
+def test_config_table_matches_library(lib):
+    import ctypes
+    rows = build.config_table()
+    assert len(rows) == lib.ctv_num_configs()
+    for (cid, kind, T, A, B, C) in rows:
+        t, w, h, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        assert lib.ctv_config_info(cid, ctypes.byref(t), ctypes.byref(w), ctypes.byref(h), ctypes.byref(nt)) == 0
+        assert t.value == T
+        if kind == 0:
+            assert (w.value, h.value, nt.value) == (A, B, C)
+        else:
+            assert (w.value, h.value, nt.value) == (32 * A, B * C, 32 * A * B)

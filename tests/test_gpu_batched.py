@@ -33,7 +33,7 @@ def plan_images(imgs, lams, types, rects=None):
     return out
 
 
-@pytest.mark.parametrize("config", [row[0] for row in __import__("paper_2109_05496_gb300.build", fromlist=["x"]).config_table()])
+@pytest.mark.parametrize("config", [2, 7, 11, 14])
 def test_plan_matches_oracle_and_loop(config):
     shapes, lams, types, imgs = make_batch(14, 3, 150, seed=5)
     ims = plan_images(imgs, lams, types)
@@ -89,3 +89,9 @@ def test_plan_full_workload_sampled():
         tv = TV_NAMES[int(types[i])]
         x1 = ctv.denoise(ims[i]["b"], float(lams[i]), tv, 100, ims[i]["C"], 0.5, config=info["config"])
         assert torch.equal(x1, ims[i]["x"])
+
+
+def test_plan_rejects_unsupported_configuration():
+    shapes, lams, types, imgs = make_batch(2, 20, 40, seed=3)
+    with pytest.raises(RuntimeError):
+        ctv.Plan(plan_images(imgs, lams, types), 10, config=5)

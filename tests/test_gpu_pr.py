@@ -178,3 +178,28 @@ def test_ip_comparator_is_projected_error_reduction():
         u, w = oPC(v.real, v.imag, OC(amp_max=1.0))
         x = torch.complex(u, w)
     assert np.abs(xg.cpu().numpy() - x.numpy()).max() <= 1e-4 * np.abs(x0).max()
+
+
+def test_paper_setting_qualitative_claims():
+    # Sec. VI-A setting (256^2 pure phase object, angular spectrum at 500 nm, 5 um pixels,
+    # 5 mm, 10% Gaussian intensity noise, back-propagated start, type-I anisotropic TV,
+    # 10 FGP iterations per outer iteration). The paper reports only curves; its
+    # qualitative findings are checked: TV-based methods beat the iterative projection
+    # method, and the constrained model (CTV) converges faster early on than TV.
+    from phantoms import intensity_with_gaussian_noise, phase_object, phase_rmse
+    m = n = 256
+    H = angular_spectrum_tf(m, n, 500e-9, 5e-6, 5e-3).astype(np.complex64)
+    x_gt = phase_object(m, n, seed=31)
+    y = intensity_with_gaussian_noise(x_gt, H.astype(np.complex128), 0.1, seed=32)
+    yg, Hg = to_gpu(np.sqrt(y).astype(np.float32), H)
+    plan = ctv.PRPlan(m, n, m, n)
+    g0, _ = plan.gradient(torch.zeros(m, n, dtype=torch.complex64, device="cuda"), yg, Hg)
+    x0 = (-g0).contiguous()
+    r0 = phase_rmse(x0.cpu().numpy(), x_gt)
+    ip = phase_rmse(ctv.api.ip_solve(plan, x0, yg, Hg, 150, ctv.Constraint(amp_max=1.0)).cpu().numpy(), x_gt)
+    res = {}
+    for name, C in (("TV", ctv.NO_CONSTRAINT), ("CTV", ctv.Constraint(amp_max=1.0))):
+        res[name] = [phase_rmse(plan.solve(x0, yg, Hg, 0.005, 1.0, C, "tv1_aniso", 10, K).cpu().numpy(), x_gt)
+                     for K in (50, 150)]
+    assert res["TV"][1] < ip - 0.05 and res["CTV"][1] < ip - 0.05
+    assert res["CTV"][0] < res["TV"][0] and res["CTV"][1] < r0
