@@ -468,6 +468,299 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
   else adj_strip_body<TV, WX, WY, PPT, CONS, true>(p, smf2, red);
 }
 
+// ---------------------------------------------------------------------------
+// Reverse step streamed down the rows by independent warps: no shared memory
+// and no block barriers. A warp owns 28 columns (lanes 2..29 of a 32-column
+// window that starts two columns to the left of them) and a band of ADJS_H
+// rows, which it walks top to bottom one row per iteration, keeping in
+// registers the rows each stencil phase still needs and taking horizontal
+// neighbours from the adjacent lanes. With row i arriving, phase A
+// (x = P_C(b - lam L^T r)) runs on row i, phases B (gbar, ebar) and C (what,
+// dL/db) on row i-1 and phase D (rbar) on row i-2; the next row's loads are
+// issued before the current row is computed.
+// ---------------------------------------------------------------------------
+#ifndef ADJS_H
+#define ADJS_H 32           // rows per warp
+#endif
+#ifndef ADJS_PF
+#define ADJS_PF 1           // rows of loads issued ahead
+#endif
+#ifndef ADJS_WARPS
+#define ADJS_WARPS 4        // warps per block (adjacent column windows)
+#endif
+constexpr int ADJS_OWN = 28;    // columns owned by a warp
+#ifndef ADJS_MINB
+#define ADJS_MINB 6
+#endif
+#ifndef ADJS_UNROLL
+#define ADJS_UNROLL 1
+#endif
+constexpr int kAdjsUnroll = ADJS_UNROLL;
+
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_dn2(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// r_k, b and qbar_k = yc Y + rc rbar_{k+1} of one pixel (zero outside the image)
+__device__ __forceinline__ void adjs_load(const AdjParams& p, long long o, bool in, float4& R, float2& B,
+                                          float4& Q) {
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  R = z4;
+  B = make_float2(0.f, 0.f);
+  Q = z4;
+  if (in) {
+    if (p.r != nullptr) R = __ldg(p.r + o);
+    B = __ldg(p.b + o);
+    if (p.Y != nullptr) {
+      const float4 y = __ldg(p.Y + o);
+      Q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
+    }
+    if (p.rbn != nullptr) {
+      const float4 y = __ldg(p.rbn + o);
+      Q = f4(Q.x + p.rc * y.x, Q.y + p.rc * y.y, Q.z + p.rc * y.z, Q.w + p.rc * y.w);
+    }
+  }
+}
+
+// Registers a warp carries down its band: row i-1 for phases B and C, row i-2
+// for phase D, and r1 of row i-1 for phase A.
+struct AdjsState {
+  float4 Rm, Qm, gbmm;
+  float2 r1p, wm, dm, xm, e2m, eb1m, whmm, d2mm;
+  float lacc;
+};
+
+// Phases A-D for arriving row i with inputs R = r_k, B = b, Q = qbar_k of row
+// i and bbo = dL/db of row i-1. EDGE = false: the warp's 32 columns lie in
+// [0, n - 1) and rows j0 - 2 .. j1 + 1 in [0, m - 1), so no bounds or edge
+// tests are needed.
+template <int TV, int CONS, bool EDGE>
+__device__ __forceinline__ void adjs_row(const AdjParams& p, AdjsState& S, int i, const float4 R, const float2 B,
+                                         const float4 Q, const float2 bbo, bool colin, bool own, bool kin,
+                                         bool has_right, int gk, int j0, int j1, long long col, float lam,
+                                         float c8) {
+  const int m = p.m, n = p.n;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const float2 z2 = make_float2(0.f, 0.f);
+  const bool rin = colin && (!EDGE || (unsigned)i < (unsigned)m);
+  const int im = i - 1;
+  const bool inm = colin && (!EDGE || (unsigned)im < (unsigned)m);
+  const bool own_m = own && im >= j0 && im < j1;
+  // A (row i): d = L^T r, w = b - lam d, x = P_C(w); e2 = x - x(right)
+  const float2 left = shfl_up2(make_float2(R.z, R.w));
+  float2 d = z2, w = z2, x = z2;
+  if (rin) {
+    d = make_float2(R.x - S.r1p.x + R.z - left.x, R.y - S.r1p.y + R.w - left.y);
+    w = make_float2(B.x - lam * d.x, B.y - lam * d.y);
+    x = proj_C_t<CONS>(w, i, gk, kin, p.C);
+  }
+  const float2 xr = shfl_dn2(x);
+  const float2 e2 = rin && has_right ? make_float2(x.x - xr.x, x.y - xr.y) : z2;
+  // B (row i-1): g = r + L x / (8 lam), gbar = J_PS(g)^T qbar, ebar = gbar / (8 lam)
+  float4 gb = z4;
+  if (inm) {
+    const float2 e1 = !EDGE || im < m - 1 ? make_float2(S.xm.x - x.x, S.xm.y - x.y) : z2;
+    const float4 g = f4(S.Rm.x + c8 * e1.x, S.Rm.y + c8 * e1.y, S.Rm.z + c8 * S.e2m.x, S.Rm.w + c8 * S.e2m.y);
+    gb = proj_S_adj<TV>(g, S.Qm, p.alpha);
+    if (EDGE && im == m - 1) { gb.x = 0.f; gb.y = 0.f; }
+    if (!has_right) { gb.z = 0.f; gb.w = 0.f; }
+    if (own_m) S.lacc -= 8.f * c8 * c8 * (gb.x * e1.x + gb.y * e1.y + gb.z * S.e2m.x + gb.w * S.e2m.y);
+  }
+  const float2 eb1 = make_float2(c8 * gb.x, c8 * gb.y), eb2 = make_float2(c8 * gb.z, c8 * gb.w);
+  // C (row i-1): xbar = L^T ebar, what = J_PC(w)^T xbar, dL/db += what
+  const float2 ebl = shfl_up2(eb2);
+  float2 wh = z2;
+  if (inm) {
+    const float2 xb = make_float2(eb1.x - S.eb1m.x + eb2.x - ebl.x, eb1.y - S.eb1m.y + eb2.y - ebl.y);
+    wh = proj_C_adj_t<CONS>(S.wm, xb, im, gk, kin, p.C);
+    if (own_m) {
+      p.bbar[col + (long long)im * n] = make_float2(bbo.x + wh.x, bbo.y + wh.y);
+      S.lacc -= S.dm.x * wh.x + S.dm.y * wh.y;
+    }
+  }
+  const float2 whr = shfl_dn2(wh);
+  const float2 d2 = inm && has_right ? make_float2(wh.x - whr.x, wh.y - whr.y) : z2;
+  // D (row i-2): rbar = gbar - lam L what
+  const int i2 = i - 2;
+  if (own && i2 >= j0 && i2 < j1) {
+    const float2 d1 = !EDGE || i2 < m - 1 ? make_float2(S.whmm.x - wh.x, S.whmm.y - wh.y) : z2;
+    p.rb_out[col + (long long)i2 * n] =
+        f4(S.gbmm.x - lam * d1.x, S.gbmm.y - lam * d1.y, S.gbmm.z - lam * S.d2mm.x, S.gbmm.w - lam * S.d2mm.y);
+  }
+  S.r1p = make_float2(R.x, R.y);
+  S.Rm = R;
+  S.Qm = Q;
+  S.wm = w;
+  S.dm = d;
+  S.xm = x;
+  S.e2m = e2;
+  S.eb1m = eb1;
+  S.gbmm = gb;
+  S.whmm = wh;
+  S.d2mm = d2;
+}
+
+__device__ __forceinline__ void adjs_init(const AdjParams& p, AdjsState& S, bool colin, bool edge, int j0,
+                                          long long col) {
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const float2 z2 = make_float2(0.f, 0.f);
+  S.Rm = S.Qm = S.gbmm = z4;
+  S.r1p = S.wm = S.dm = S.xm = S.e2m = S.eb1m = S.whmm = S.d2mm = z2;
+  S.lacc = 0.f;
+  // r1 of row j0-2 (upper neighbour of the first row phase A computes)
+  if (p.r != nullptr && colin && (!edge || j0 - 2 >= 0)) {
+    const float4 t = __ldg(p.r + col + (long long)(j0 - 2) * p.n);
+    S.r1p = make_float2(t.x, t.y);
+  }
+}
+
+// Band with register prefetch of the next row.
+template <int TV, int CONS, bool EDGE>
+__device__ __forceinline__ float adjs_band(const AdjParams& p, int lane, int gk, int j0, int j1, long long col,
+                                           float lam, float c8) {
+  const int m = p.m, n = p.n;
+  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
+  const bool own = colin && lane >= 2 && lane < 2 + ADJS_OWN;
+  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
+  const bool has_right = !EDGE || gk < n - 1;
+  AdjsState S;
+  adjs_init(p, S, colin, EDGE, j0, col);
+  float4 Rn, Qn;
+  float2 Bn;
+  adjs_load(p, col + (long long)(j0 - 1) * n, colin && (!EDGE || (unsigned)(j0 - 1) < (unsigned)m), Rn, Bn, Qn);
+  float2 bbn = make_float2(0.f, 0.f);   // dL/db of row i-1, loaded one iteration ahead
+#pragma unroll kAdjsUnroll
+  for (int i = j0 - 1; i <= j1 + 1; ++i) {
+    const float4 R = Rn, Q = Qn;
+    const float2 B = Bn;
+    if (i <= j1)
+      adjs_load(p, col + (long long)(i + 1) * n, colin && (!EDGE || (unsigned)(i + 1) < (unsigned)m), Rn, Bn, Qn);
+    const float2 bbo = bbn;
+    bbn = own && i >= j0 && i < j1 ? p.bbar[col + (long long)i * n] : make_float2(0.f, 0.f);
+    adjs_row<TV, CONS, EDGE>(p, S, i, R, B, Q, bbo, colin, own, kin, has_right, gk, j0, j1, col, lam, c8);
+  }
+  return S.lacc;
+}
+
+// Band with asynchronous copies (cp.async) of the next ADJS_D - 1 rows into a
+// per-warp ring of shared-memory slots: the loads are in flight for several
+// rows without holding registers. Every lane reads back only its own column.
+#ifndef ADJS_D
+#define ADJS_D 4            // ring slots (rows in flight + the row being consumed)
+#endif
+struct AdjsSlot {
+  float4 R[32], Y[32], N[32];
+  float2 B[32], BB[32];
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the copies of row gj (zero-filled outside the image; dL/db only for
+// owned pixels of the band) and close the group.
+__device__ __forceinline__ void adjs_issue(const AdjParams& p, AdjsSlot* sl, int lane, int gj, bool colin, bool own,
+                                          int j0, int j1, long long col) {
+  const bool in = colin && (unsigned)gj < (unsigned)p.m;
+  const long long o = in ? col + (long long)gj * p.n : 0;
+  const int s16 = in ? 16 : 0, s8 = in ? 8 : 0;
+  if (p.r != nullptr) cp_async16(&sl->R[lane], p.r + o, s16);
+  cp_async8(&sl->B[lane], p.b + o, s8);
+  if (p.Y != nullptr) cp_async16(&sl->Y[lane], p.Y + o, s16);
+  if (p.rbn != nullptr) cp_async16(&sl->N[lane], p.rbn + o, s16);
+  const bool bo = own && gj >= j0 && gj < j1;
+  cp_async8(&sl->BB[lane], p.bbar + (bo ? o : 0), bo ? 8 : 0);
+  cp_async_commit();
+}
+
+template <int TV, int CONS, bool EDGE>
+__device__ __forceinline__ float adjs_band_async(const AdjParams& p, AdjsSlot* ring, int lane, int gk, int j0,
+                                                 int j1, long long col, float lam, float c8) {
+  const int n = p.n;
+  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
+  const bool own = colin && lane >= 2 && lane < 2 + ADJS_OWN;
+  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
+  const bool has_right = !EDGE || gk < n - 1;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  AdjsState S;
+  adjs_init(p, S, colin, EDGE, j0, col);
+  // prologue: rows j0-1 .. j0+D-3 in slots 0 .. D-2
+#pragma unroll
+  for (int t = 0; t < ADJS_D - 1; ++t) adjs_issue(p, ring + t, lane, j0 - 1 + t, colin, own, j0, j1, col);
+  float2 bbn = make_float2(0.f, 0.f);
+  int slot = 0;
+  for (int i = j0 - 1; i <= j1 + 1; ++i) {
+    // refill the slot consumed last iteration with row i+D-1 (an empty group past the band)
+    const int fill = slot == 0 ? ADJS_D - 1 : slot - 1;
+    if (i + ADJS_D - 1 <= j1 + 1) adjs_issue(p, ring + fill, lane, i + ADJS_D - 1, colin, own, j0, j1, col);
+    else cp_async_commit();
+    cp_async_wait<ADJS_D - 1>();
+    const AdjsSlot* sl = ring + slot;
+    const float4 R = p.r != nullptr ? sl->R[lane] : z4;
+    const float2 B = sl->B[lane];
+    float4 Q = z4;
+    if (p.Y != nullptr) {
+      const float4 y = sl->Y[lane];
+      Q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
+    }
+    if (p.rbn != nullptr) {
+      const float4 y = sl->N[lane];
+      Q = f4(Q.x + p.rc * y.x, Q.y + p.rc * y.y, Q.z + p.rc * y.z, Q.w + p.rc * y.w);
+    }
+    const float2 bbo = bbn;
+    bbn = sl->BB[lane];
+    adjs_row<TV, CONS, EDGE>(p, S, i, R, B, Q, bbo, colin, own, kin, has_right, gk, j0, j1, col, lam, c8);
+    slot = slot == ADJS_D - 1 ? 0 : slot + 1;
+  }
+  cp_async_wait<0>();
+  return S.lacc;
+}
+
+#ifndef CTV_ADJ_ASYNC
+#define CTV_ADJ_ASYNC 1
+#endif
+
+template <int TV, int CONS>
+__global__ void __launch_bounds__(32 * ADJS_WARPS, ADJS_MINB) adj_stream_kernel(AdjParams p) {
+  const int lane = threadIdx.x & 31;
+  const int wc = blockIdx.x * ADJS_WARPS + (threadIdx.x >> 5);
+  const int m = p.m, n = p.n;
+  if (wc * ADJS_OWN >= n) return;   // whole warp past the last column
+  const int z = blockIdx.z;
+  const float lam = fmaxf(p.lam_dev[z], 0.f);
+  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
+  const int gk0 = wc * ADJS_OWN - 2;
+  const int gk = gk0 + lane;
+  const int j0 = blockIdx.y * ADJS_H;
+  const int j1 = min(j0 + ADJS_H, m);
+  const long long col = (long long)z * p.px + gk;
+  const bool inside = gk0 >= 0 && gk0 + 32 <= n - 1 && j0 - 2 >= 0 && j1 + 2 <= m - 1;
+#if CTV_ADJ_ASYNC
+  extern __shared__ AdjsSlot adjs_ring[];
+  AdjsSlot* ring = adjs_ring + (threadIdx.x >> 5) * ADJS_D;
+  const float lacc = inside ? adjs_band_async<TV, CONS, false>(p, ring, lane, gk, j0, j1, col, lam, c8)
+                            : adjs_band_async<TV, CONS, true>(p, ring, lane, gk, j0, j1, col, lam, c8);
+#else
+  const float lacc = inside ? adjs_band<TV, CONS, false>(p, lane, gk, j0, j1, col, lam, c8)
+                            : adjs_band<TV, CONS, true>(p, lane, gk, j0, j1, col, lam, c8);
+#endif
+  double v = (double)lacc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) atomicAdd(p.lamacc + z, v);
+}
+
 // reverse-step geometry: warps across, warps down, rows per thread
 #ifndef CTV_ADJ_CFG
 #define CTV_ADJ_CFG 4
@@ -503,14 +796,57 @@ static cudaError_t launch_adj_strip_tv(int cons, const AdjParams& p, int batch, 
   }
 }
 
+template <int TV, int CONS>
+static cudaError_t launch_adj_stream_t(const AdjParams& p, int batch, cudaStream_t s) {
+  const int ncw = (p.n + ADJS_OWN - 1) / ADJS_OWN;
+  dim3 grid((ncw + ADJS_WARPS - 1) / ADJS_WARPS, (p.m + ADJS_H - 1) / ADJS_H, batch);
+#if CTV_ADJ_ASYNC
+  constexpr size_t smem = sizeof(AdjsSlot) * ADJS_D * ADJS_WARPS;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(adj_stream_kernel<TV, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+#else
+  constexpr size_t smem = 0;
+#endif
+  adj_stream_kernel<TV, CONS><<<grid, 32 * ADJS_WARPS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TV>
+static cudaError_t launch_adj_stream_tv(int cons, const AdjParams& p, int batch, cudaStream_t s) {
+  switch (cons) {
+    case CONS_NONE: return launch_adj_stream_t<TV, CONS_NONE>(p, batch, s);
+    case CONS_AMP: return launch_adj_stream_t<TV, CONS_AMP>(p, batch, s);
+    case CONS_RECT: return launch_adj_stream_t<TV, CONS_RECT>(p, batch, s);
+    default: return launch_adj_stream_t<TV, CONS_GEN>(p, batch, s);
+  }
+}
+
+#ifndef CTV_ADJ_STREAM
+#define CTV_ADJ_STREAM 1
+#endif
+
 static cudaError_t launch_adj_step(int tv, const AdjParams& p, int batch, cudaStream_t s) {
   const int cons = cons_mode(p.C);
+#if CTV_ADJ_STREAM
+  switch (tv) {
+    case TV1_ISO: return launch_adj_stream_tv<TV1_ISO>(cons, p, batch, s);
+    case TV1_ANISO: return launch_adj_stream_tv<TV1_ANISO>(cons, p, batch, s);
+    case TV2_ISO: return launch_adj_stream_tv<TV2_ISO>(cons, p, batch, s);
+    default: return launch_adj_stream_tv<TV2_ANISO>(cons, p, batch, s);
+  }
+#else
   switch (tv) {
     case TV1_ISO: return launch_adj_strip_tv<TV1_ISO>(cons, p, batch, s);
     case TV1_ANISO: return launch_adj_strip_tv<TV1_ANISO>(cons, p, batch, s);
     case TV2_ISO: return launch_adj_strip_tv<TV2_ISO>(cons, p, batch, s);
     default: return launch_adj_strip_tv<TV2_ANISO>(cons, p, batch, s);
   }
+#endif
 }
 
 static cudaError_t launch_adj_final(int tv, const AdjParams& p, int batch, cudaStream_t s) {
