@@ -17,10 +17,12 @@
 //     rbar_k = gbar - lam L what
 // Each segment of ckpt_every iterations is first recomputed from its
 // checkpoint by the fused pass, storing every r_k of the segment, then walked
-// backwards one reverse step per launch (adj_strip_kernel: a two-pixel halo,
-// since the reverse step reads two stencils deep). (Running the next segment's
-// recompute on a second stream during the walk back was measured: both kernels
-// fill the GPU, so it saved nothing.) All Jacobians are those of the projections, which
+// backwards two reverse steps per launch (adj2_stream_kernel; a single step,
+// adj_stream_kernel, where a segment has an odd number left). Both kernels
+// stream warps down bands of rows with a two-pixel halo per step, since a
+// reverse step reads two stencils deep. (Running the next segment's recompute
+// on a second stream during the walk back was measured: both kernels fill the
+// GPU, so it saved nothing.) All Jacobians are those of the projections, which
 // are symmetric; at a projection's boundary the interior branch (identity) is
 // taken, and the projection onto a radius-0 ball has Jacobian 0.
 #include <cuda_runtime.h>
@@ -81,6 +83,17 @@ __device__ __forceinline__ float2 proj_C_adj_t(float2 w, float2 xb, int gj, int 
   return proj_C_adj(w, xb, gj, gk, c);
 }
 
+// qbar_k = yc Y + rc rbar_{k+1} and the running dL/db sum with a fixed rounding
+// sequence (yc Y rounded, then one FMA; plain rounded adds), so that every
+// reverse-step kernel, whatever the compiler fuses around it, gives the same bits
+__device__ __forceinline__ float4 q_scale(float c, float4 y) {
+  return f4(__fmul_rn(c, y.x), __fmul_rn(c, y.y), __fmul_rn(c, y.z), __fmul_rn(c, y.w));
+}
+__device__ __forceinline__ float4 q_axpy(float c, float4 y, float4 q) {
+  return f4(__fmaf_rn(c, y.x, q.x), __fmaf_rn(c, y.y, q.y), __fmaf_rn(c, y.z, q.z), __fmaf_rn(c, y.w, q.w));
+}
+__device__ __forceinline__ float2 add_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+
 // (a, b) <- J^T (a, b) for the projection of the pair (u, v) onto the ball of radius rad
 __device__ __forceinline__ void ball2_adj(float u, float v, float rad, float& a, float& b) {
   if (rad <= 0.f) { a = 0.f; b = 0.f; return; }
@@ -132,6 +145,12 @@ struct AdjParams {
   const float4* rbn;      // rbar_{k+1} (nullptr: 0)
   float rc;               // 1 + beta_k
   float4* rb_out;         // rbar_k
+  // two-step reverse pass only: step k-1, whose carry is rbn (coefficient
+  // -beta_k) and whose rbar_{k+1} is the rbar_k computed in the same pass
+  const float4* r_lo;     // r_{k-1} (nullptr: 0)
+  float yc_lo;            // -beta_k
+  float rc_lo;            // 1 + beta_{k-1}
+  float4* rb_out_lo;      // rbar_{k-1}
   const float2* xbar;     // finalize only
   const float4* qK;       // finalize only
   float4* qbK;            // finalize only: qbar_K
@@ -294,180 +313,6 @@ static bool hist_config_ok(int cfg) {
   return false;
 }
 
-// Reverse step with column-strip ownership (same arithmetic as adj_step_kernel):
-// a warp covers 32 columns, each thread PPT consecutive rows of its column, so
-// the vertical neighbours of the four stencil phases come from registers except
-// at strip ends. Region 32 WX x PPT WY with a two-pixel halo.
-template <int TV, int WX, int WY, int PPT, int CONS, bool EDGE>
-__device__ __forceinline__ void adj_strip_body(const AdjParams& p, float2* smf2, double* red) {
-  constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH, NT = 32 * WX * WY;
-  float2* S2 = smf2;          // p2 of r (phase A), then p2 of ebar (phases B-C)
-  float2* XW = S2 + R;        // x (A-B), then what (C-D)
-  float2* B1 = XW + R;        // strip-bottom p1 of r (A), then of ebar (B-C)
-  const int z = blockIdx.z;
-  const long long off = (long long)z * p.px;
-  const float lam = fmaxf(p.lam_dev[z], 0.f);
-  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
-  const int m = p.m, n = p.n;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wx = warp % WX, wy = warp / WX;
-  const int lk = wx * 32 + lane, lj0 = wy * PPT;
-  const int gk = blockIdx.x * (RW - 4) - 2 + lk;
-  const int gj0 = blockIdx.y * (RH - 4) - 2 + lj0;
-  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
-  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
-  const bool kint = lk >= 2 && lk < RW - 2;
-  const bool right_in = lk < RW - 1 && (!EDGE || gk < n - 1);
-  const bool strip_next = lj0 + PPT < RH;
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  const float2 z2 = make_float2(0.f, 0.f);
-  float4 r[PPT], qb[PPT], gb[PPT];
-  float2 bb[PPT], dd[PPT], ww[PPT], xx[PPT], e1[PPT], e2[PPT], ba[PPT];
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int gj = gj0 + s;
-    r[s] = z4;
-    qb[s] = z4;
-    bb[s] = z2;
-    ba[s] = z2;
-    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
-      const long long o = off + (long long)gj * n + gk;
-      if (p.r != nullptr) r[s] = __ldg(p.r + o);
-      bb[s] = __ldg(p.b + o);
-      if (kint && lj0 + s >= 2 && lj0 + s < RH - 2) ba[s] = p.bbar[o];   // running dL/db, updated in phase C
-      float4 q = z4;
-      if (p.Y != nullptr) {
-        const float4 y = __ldg(p.Y + o);
-        q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
-      }
-      if (p.rbn != nullptr) {
-        const float4 y = __ldg(p.rbn + o);
-        q = f4(q.x + p.rc * y.x, q.y + p.rc * y.y, q.z + p.rc * y.z, q.w + p.rc * y.w);
-      }
-      qb[s] = q;
-    }
-    S2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
-  }
-  B1[wy * RW + lk] = make_float2(r[PPT - 1].x, r[PPT - 1].y);
-  __syncthreads();
-  // A: d = L^T r, w = b - lam d, x = P_C(w)
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int gj = gj0 + s;
-    dd[s] = z2;
-    ww[s] = z2;
-    xx[s] = z2;
-    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
-      float2 up;
-      if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
-      else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
-      const float2 left = lk > 0 ? S2[(lj0 + s) * RW + lk - 1] : z2;
-      dd[s] = make_float2(r[s].x - up.x + r[s].z - left.x, r[s].y - up.y + r[s].w - left.y);
-      ww[s] = make_float2(bb[s].x - lam * dd[s].x, bb[s].y - lam * dd[s].y);
-      xx[s] = proj_C_t<CONS>(ww[s], gj, gk, kin, p.C);
-    }
-    XW[(lj0 + s) * RW + lk] = xx[s];
-  }
-  __syncthreads();
-  // B: e = L x, g = r + e/(8 lam), gbar = J_PS(g)^T qbar, ebar = gbar/(8 lam)
-  float lacc = 0.f;
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int gj = gj0 + s;
-    gb[s] = z4;
-    e1[s] = z2;
-    e2[s] = z2;
-    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
-      float ea = 0.f, eb_ = 0.f, ec = 0.f, ed = 0.f;
-      if (!EDGE || gj < m - 1) {
-        float2 xd;
-        if (s < PPT - 1) xd = xx[s + 1];
-        else xd = strip_next ? XW[(lj0 + s + 1) * RW + lk] : xx[s];
-        ea = xx[s].x - xd.x;
-        eb_ = xx[s].y - xd.y;
-      }
-      if (right_in) {
-        const float2 xr = XW[(lj0 + s) * RW + lk + 1];
-        ec = xx[s].x - xr.x;
-        ed = xx[s].y - xr.y;
-      }
-      const float4 g = f4(r[s].x + c8 * ea, r[s].y + c8 * eb_, r[s].z + c8 * ec, r[s].w + c8 * ed);
-      float4 gbar = proj_S_adj<TV>(g, qb[s], p.alpha);
-      if (EDGE && gj == m - 1) { gbar.x = 0.f; gbar.y = 0.f; }
-      if (EDGE && gk == n - 1) { gbar.z = 0.f; gbar.w = 0.f; }
-      gb[s] = gbar;
-      e1[s] = make_float2(c8 * gbar.x, c8 * gbar.y);
-      e2[s] = make_float2(c8 * gbar.z, c8 * gbar.w);
-      const int lj = lj0 + s;
-      if (kint && lj >= 2 && lj < RH - 2)
-        lacc -= 8.f * c8 * c8 * (gbar.x * ea + gbar.y * eb_ + gbar.z * ec + gbar.w * ed);
-    }
-    // phase A's reads of S2 and B1 all happened before the last barrier
-    S2[(lj0 + s) * RW + lk] = e2[s];
-  }
-  B1[wy * RW + lk] = e1[PPT - 1];
-  __syncthreads();
-  // C: xbar = L^T ebar, what = J_PC(w)^T xbar; bbar += what
-#pragma unroll
-  for (int s = 0; s < PPT; ++s) {
-    const int gj = gj0 + s;
-    float2 wh = z2;
-    if (colin && (!EDGE || (unsigned)gj < (unsigned)m)) {
-      float2 up;
-      if (s > 0) up = e1[s - 1];
-      else up = wy > 0 ? B1[(wy - 1) * RW + lk] : z2;
-      const float2 left = lk > 0 ? S2[(lj0 + s) * RW + lk - 1] : z2;
-      const float2 xb = make_float2(e1[s].x - up.x + e2[s].x - left.x, e1[s].y - up.y + e2[s].y - left.y);
-      wh = proj_C_adj_t<CONS>(ww[s], xb, gj, gk, kin, p.C);
-      const int lj = lj0 + s;
-      if (kint && lj >= 2 && lj < RH - 2) {
-        p.bbar[off + (long long)gj * n + gk] = make_float2(ba[s].x + wh.x, ba[s].y + wh.y);
-        lacc -= dd[s].x * wh.x + dd[s].y * wh.y;
-      }
-    }
-    xx[s] = wh;
-    XW[(lj0 + s) * RW + lk] = wh;
-  }
-  __syncthreads();
-  // D: rbar_k = gbar - lam L what
-  if (kint && colin) {
-#pragma unroll
-    for (int s = 0; s < PPT; ++s) {
-      const int lj = lj0 + s, gj = gj0 + s;
-      if (lj >= 2 && lj < RH - 2 && (!EDGE || (unsigned)gj < (unsigned)m)) {
-        float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-        if (!EDGE || gj < m - 1) {
-          const float2 wd = s < PPT - 1 ? xx[s + 1] : XW[(lj0 + s + 1) * RW + lk];
-          d1r = xx[s].x - wd.x;
-          d1i = xx[s].y - wd.y;
-        }
-        if (!EDGE || gk < n - 1) {
-          const float2 wr = XW[(lj0 + s) * RW + lk + 1];
-          d2r = xx[s].x - wr.x;
-          d2i = xx[s].y - wr.y;
-        }
-        p.rb_out[off + (long long)gj * n + gk] =
-            f4(gb[s].x - lam * d1r, gb[s].y - lam * d1i, gb[s].z - lam * d2r, gb[s].w - lam * d2i);
-      }
-    }
-  }
-  double v[1] = {(double)lacc};
-  block_sum<NT, 1>(v, red);
-  if (tid == 0) atomicAdd(p.lamacc + z, v[0]);
-}
-
-template <int TV, int WX, int WY, int PPT, int CONS>
-__global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
-  constexpr int RW = 32 * WX, RH = PPT * WY;
-  extern __shared__ float2 smf2[];
-  __shared__ double red[WX * WY];
-  const int gj0 = blockIdx.y * (RH - 4) - 2, gk0 = blockIdx.x * (RW - 4) - 2;
-  // fast path for regions inside the image away from its last row and column
-  const bool inside = gj0 >= 0 && gk0 >= 0 && gj0 + RH <= p.m - 1 && gk0 + RW <= p.n - 1;
-  if (inside) adj_strip_body<TV, WX, WY, PPT, CONS, false>(p, smf2, red);
-  else adj_strip_body<TV, WX, WY, PPT, CONS, true>(p, smf2, red);
-}
-
 // ---------------------------------------------------------------------------
 // Reverse step streamed down the rows by independent warps: no shared memory
 // and no block barriers. A warp owns 28 columns (lanes 2..29 of a 32-column
@@ -480,7 +325,7 @@ __global__ void __launch_bounds__(32 * WX * WY) adj_strip_kernel(AdjParams p) {
 // issued before the current row is computed.
 // ---------------------------------------------------------------------------
 #ifndef ADJS_H
-#define ADJS_H 32           // rows per warp
+#define ADJS_H 16           // rows per warp
 #endif
 #ifndef ADJS_PF
 #define ADJS_PF 1           // rows of loads issued ahead
@@ -492,37 +337,12 @@ constexpr int ADJS_OWN = 28;    // columns owned by a warp
 #ifndef ADJS_MINB
 #define ADJS_MINB 6
 #endif
-#ifndef ADJS_UNROLL
-#define ADJS_UNROLL 1
-#endif
-constexpr int kAdjsUnroll = ADJS_UNROLL;
 
 __device__ __forceinline__ float2 shfl_up2(float2 v) {
   return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
 }
 __device__ __forceinline__ float2 shfl_dn2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
-}
-
-// r_k, b and qbar_k = yc Y + rc rbar_{k+1} of one pixel (zero outside the image)
-__device__ __forceinline__ void adjs_load(const AdjParams& p, long long o, bool in, float4& R, float2& B,
-                                          float4& Q) {
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  R = z4;
-  B = make_float2(0.f, 0.f);
-  Q = z4;
-  if (in) {
-    if (p.r != nullptr) R = __ldg(p.r + o);
-    B = __ldg(p.b + o);
-    if (p.Y != nullptr) {
-      const float4 y = __ldg(p.Y + o);
-      Q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
-    }
-    if (p.rbn != nullptr) {
-      const float4 y = __ldg(p.rbn + o);
-      Q = f4(Q.x + p.rc * y.x, Q.y + p.rc * y.y, Q.z + p.rc * y.z, Q.w + p.rc * y.w);
-    }
-  }
 }
 
 // Registers a warp carries down its band: row i-1 for phases B and C, row i-2
@@ -534,21 +354,21 @@ struct AdjsState {
 };
 
 // Phases A-D for arriving row i with inputs R = r_k, B = b, Q = qbar_k of row
-// i and bbo = dL/db of row i-1. EDGE = false: the warp's 32 columns lie in
-// [0, n - 1) and rows j0 - 2 .. j1 + 1 in [0, m - 1), so no bounds or edge
-// tests are needed.
+// i: what of row i-1 and rbar of row i-2 are returned (rbar computed on every
+// lane and row; only the caller knows which are valid and owned); own_m says
+// whether row i-1 of this lane counts toward dL/dlambda. EDGE = false: the
+// warp's 32 columns lie in [0, n - 1) and the rows in [0, m - 1), so no bounds
+// or edge tests are needed.
 template <int TV, int CONS, bool EDGE>
-__device__ __forceinline__ void adjs_row(const AdjParams& p, AdjsState& S, int i, const float4 R, const float2 B,
-                                         const float4 Q, const float2 bbo, bool colin, bool own, bool kin,
-                                         bool has_right, int gk, int j0, int j1, long long col, float lam,
-                                         float c8) {
-  const int m = p.m, n = p.n;
+__device__ __forceinline__ void adjs_core(const AdjParams& p, AdjsState& S, int i, const float4 R, const float2 B,
+                                          const float4 Q, bool colin, bool own_m, bool kin, bool has_right, int gk,
+                                          float lam, float c8, float2& wh_out, float4& rbar_out) {
+  const int m = p.m;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
   const bool rin = colin && (!EDGE || (unsigned)i < (unsigned)m);
   const int im = i - 1;
   const bool inm = colin && (!EDGE || (unsigned)im < (unsigned)m);
-  const bool own_m = own && im >= j0 && im < j1;
   // A (row i): d = L^T r, w = b - lam d, x = P_C(w); e2 = x - x(right)
   const float2 left = shfl_up2(make_float2(R.z, R.w));
   float2 d = z2, w = z2, x = z2;
@@ -570,26 +390,20 @@ __device__ __forceinline__ void adjs_row(const AdjParams& p, AdjsState& S, int i
     if (own_m) S.lacc -= 8.f * c8 * c8 * (gb.x * e1.x + gb.y * e1.y + gb.z * S.e2m.x + gb.w * S.e2m.y);
   }
   const float2 eb1 = make_float2(c8 * gb.x, c8 * gb.y), eb2 = make_float2(c8 * gb.z, c8 * gb.w);
-  // C (row i-1): xbar = L^T ebar, what = J_PC(w)^T xbar, dL/db += what
+  // C (row i-1): xbar = L^T ebar, what = J_PC(w)^T xbar
   const float2 ebl = shfl_up2(eb2);
   float2 wh = z2;
   if (inm) {
     const float2 xb = make_float2(eb1.x - S.eb1m.x + eb2.x - ebl.x, eb1.y - S.eb1m.y + eb2.y - ebl.y);
     wh = proj_C_adj_t<CONS>(S.wm, xb, im, gk, kin, p.C);
-    if (own_m) {
-      p.bbar[col + (long long)im * n] = make_float2(bbo.x + wh.x, bbo.y + wh.y);
-      S.lacc -= S.dm.x * wh.x + S.dm.y * wh.y;
-    }
+    if (own_m) S.lacc -= S.dm.x * wh.x + S.dm.y * wh.y;
   }
   const float2 whr = shfl_dn2(wh);
   const float2 d2 = inm && has_right ? make_float2(wh.x - whr.x, wh.y - whr.y) : z2;
   // D (row i-2): rbar = gbar - lam L what
-  const int i2 = i - 2;
-  if (own && i2 >= j0 && i2 < j1) {
-    const float2 d1 = !EDGE || i2 < m - 1 ? make_float2(S.whmm.x - wh.x, S.whmm.y - wh.y) : z2;
-    p.rb_out[col + (long long)i2 * n] =
-        f4(S.gbmm.x - lam * d1.x, S.gbmm.y - lam * d1.y, S.gbmm.z - lam * S.d2mm.x, S.gbmm.w - lam * S.d2mm.y);
-  }
+  const float2 d1 = !EDGE || i - 2 < m - 1 ? make_float2(S.whmm.x - wh.x, S.whmm.y - wh.y) : z2;
+  rbar_out = f4(S.gbmm.x - lam * d1.x, S.gbmm.y - lam * d1.y, S.gbmm.z - lam * S.d2mm.x, S.gbmm.w - lam * S.d2mm.y);
+  wh_out = wh;
   S.r1p = make_float2(R.x, R.y);
   S.Rm = R;
   S.Qm = Q;
@@ -603,53 +417,42 @@ __device__ __forceinline__ void adjs_row(const AdjParams& p, AdjsState& S, int i
   S.d2mm = d2;
 }
 
-__device__ __forceinline__ void adjs_init(const AdjParams& p, AdjsState& S, bool colin, bool edge, int j0,
-                                          long long col) {
+// One reverse step on arriving row i: dL/db of row i-1 (bbo: its value before
+// this step) and rbar_k of row i-2 are written for the owned pixels of the band.
+template <int TV, int CONS, bool EDGE>
+__device__ __forceinline__ void adjs_row(const AdjParams& p, AdjsState& S, int i, const float4 R, const float2 B,
+                                         const float4 Q, const float2 bbo, bool colin, bool own, bool kin,
+                                         bool has_right, int gk, int j0, int j1, long long col, float lam,
+                                         float c8) {
+  const int n = p.n;
+  const int im = i - 1, i2 = i - 2;
+  const bool own_m = own && im >= j0 && im < j1;
+  float2 wh;
+  float4 rb;
+  adjs_core<TV, CONS, EDGE>(p, S, i, R, B, Q, colin, own_m, kin, has_right, gk, lam, c8, wh, rb);
+  if (own_m) p.bbar[col + (long long)im * n] = add_rn(bbo, wh);
+  if (own && i2 >= j0 && i2 < j1) p.rb_out[col + (long long)i2 * n] = rb;
+}
+
+__device__ __forceinline__ void adjs_init(const AdjParams& p, const float4* r, AdjsState& S, bool colin, bool edge,
+                                          int j0, long long col) {
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
   S.Rm = S.Qm = S.gbmm = z4;
   S.r1p = S.wm = S.dm = S.xm = S.e2m = S.eb1m = S.whmm = S.d2mm = z2;
   S.lacc = 0.f;
   // r1 of row j0-2 (upper neighbour of the first row phase A computes)
-  if (p.r != nullptr && colin && (!edge || j0 - 2 >= 0)) {
-    const float4 t = __ldg(p.r + col + (long long)(j0 - 2) * p.n);
+  if (r != nullptr && colin && (!edge || j0 - 2 >= 0)) {
+    const float4 t = __ldg(r + col + (long long)(j0 - 2) * p.n);
     S.r1p = make_float2(t.x, t.y);
   }
-}
-
-// Band with register prefetch of the next row.
-template <int TV, int CONS, bool EDGE>
-__device__ __forceinline__ float adjs_band(const AdjParams& p, int lane, int gk, int j0, int j1, long long col,
-                                           float lam, float c8) {
-  const int m = p.m, n = p.n;
-  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
-  const bool own = colin && lane >= 2 && lane < 2 + ADJS_OWN;
-  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
-  const bool has_right = !EDGE || gk < n - 1;
-  AdjsState S;
-  adjs_init(p, S, colin, EDGE, j0, col);
-  float4 Rn, Qn;
-  float2 Bn;
-  adjs_load(p, col + (long long)(j0 - 1) * n, colin && (!EDGE || (unsigned)(j0 - 1) < (unsigned)m), Rn, Bn, Qn);
-  float2 bbn = make_float2(0.f, 0.f);   // dL/db of row i-1, loaded one iteration ahead
-#pragma unroll kAdjsUnroll
-  for (int i = j0 - 1; i <= j1 + 1; ++i) {
-    const float4 R = Rn, Q = Qn;
-    const float2 B = Bn;
-    if (i <= j1)
-      adjs_load(p, col + (long long)(i + 1) * n, colin && (!EDGE || (unsigned)(i + 1) < (unsigned)m), Rn, Bn, Qn);
-    const float2 bbo = bbn;
-    bbn = own && i >= j0 && i < j1 ? p.bbar[col + (long long)i * n] : make_float2(0.f, 0.f);
-    adjs_row<TV, CONS, EDGE>(p, S, i, R, B, Q, bbo, colin, own, kin, has_right, gk, j0, j1, col, lam, c8);
-  }
-  return S.lacc;
 }
 
 // Band with asynchronous copies (cp.async) of the next ADJS_D - 1 rows into a
 // per-warp ring of shared-memory slots: the loads are in flight for several
 // rows without holding registers. Every lane reads back only its own column.
 #ifndef ADJS_D
-#define ADJS_D 4            // ring slots (rows in flight + the row being consumed)
+#define ADJS_D 3            // ring slots (rows in flight + the row being consumed)
 #endif
 struct AdjsSlot {
   float4 R[32], Y[32], N[32];
@@ -694,7 +497,7 @@ __device__ __forceinline__ float adjs_band_async(const AdjParams& p, AdjsSlot* r
   const bool has_right = !EDGE || gk < n - 1;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   AdjsState S;
-  adjs_init(p, S, colin, EDGE, j0, col);
+  adjs_init(p, p.r, S, colin, EDGE, j0, col);
   // prologue: rows j0-1 .. j0+D-3 in slots 0 .. D-2
 #pragma unroll
   for (int t = 0; t < ADJS_D - 1; ++t) adjs_issue(p, ring + t, lane, j0 - 1 + t, colin, own, j0, j1, col);
@@ -712,11 +515,11 @@ __device__ __forceinline__ float adjs_band_async(const AdjParams& p, AdjsSlot* r
     float4 Q = z4;
     if (p.Y != nullptr) {
       const float4 y = sl->Y[lane];
-      Q = f4(p.yc * y.x, p.yc * y.y, p.yc * y.z, p.yc * y.w);
+      Q = q_scale(p.yc, y);
     }
     if (p.rbn != nullptr) {
       const float4 y = sl->N[lane];
-      Q = f4(Q.x + p.rc * y.x, Q.y + p.rc * y.y, Q.z + p.rc * y.z, Q.w + p.rc * y.w);
+      Q = q_axpy(p.rc, y, Q);
     }
     const float2 bbo = bbn;
     bbn = sl->BB[lane];
@@ -726,10 +529,6 @@ __device__ __forceinline__ float adjs_band_async(const AdjParams& p, AdjsSlot* r
   cp_async_wait<0>();
   return S.lacc;
 }
-
-#ifndef CTV_ADJ_ASYNC
-#define CTV_ADJ_ASYNC 1
-#endif
 
 template <int TV, int CONS>
 __global__ void __launch_bounds__(32 * ADJS_WARPS, ADJS_MINB) adj_stream_kernel(AdjParams p) {
@@ -746,61 +545,163 @@ __global__ void __launch_bounds__(32 * ADJS_WARPS, ADJS_MINB) adj_stream_kernel(
   const int j1 = min(j0 + ADJS_H, m);
   const long long col = (long long)z * p.px + gk;
   const bool inside = gk0 >= 0 && gk0 + 32 <= n - 1 && j0 - 2 >= 0 && j1 + 2 <= m - 1;
-#if CTV_ADJ_ASYNC
   extern __shared__ AdjsSlot adjs_ring[];
   AdjsSlot* ring = adjs_ring + (threadIdx.x >> 5) * ADJS_D;
   const float lacc = inside ? adjs_band_async<TV, CONS, false>(p, ring, lane, gk, j0, j1, col, lam, c8)
                             : adjs_band_async<TV, CONS, true>(p, ring, lane, gk, j0, j1, col, lam, c8);
-#else
-  const float lacc = inside ? adjs_band<TV, CONS, false>(p, lane, gk, j0, j1, col, lam, c8)
-                            : adjs_band<TV, CONS, true>(p, lane, gk, j0, j1, col, lam, c8);
-#endif
   double v = (double)lacc;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane == 0) atomicAdd(p.lamacc + z, v);
 }
 
-// reverse-step geometry: warps across, warps down, rows per thread
-#ifndef CTV_ADJ_CFG
-#define CTV_ADJ_CFG 4
+// ---------------------------------------------------------------------------
+// Two reverse steps (k, then k-1) in one streaming pass. Step k runs as in
+// adj_stream_kernel; step k-1 follows two rows behind, its qbar_{k-1} =
+// -beta_k rbar_{k+1} + (1 + beta_{k-1}) rbar_k taking rbar_k from step k's
+// phase D of the same iteration. Both rbar_k and rbar_{k-1} are written, and
+// dL/db is read and written once for both steps. The lower step's valid lanes
+// shrink to 3..28, so a warp owns 26 columns; the ring keeps each row's slot
+// until the lower step has read it two iterations later.
+// ---------------------------------------------------------------------------
+#ifndef CTV_ADJ_PAIR
+#define CTV_ADJ_PAIR 1
 #endif
-#if CTV_ADJ_CFG == 1
-constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 4;    // 64 x 32 region, 512 threads
-#elif CTV_ADJ_CFG == 2
-constexpr int AS_WX = 2, AS_WY = 4, AS_PPT = 4;    // 64 x 16 region, 256 threads
-#elif CTV_ADJ_CFG == 4
-constexpr int AS_WX = 1, AS_WY = 8, AS_PPT = 2;    // 32 x 16 region, 256 threads
-#elif CTV_ADJ_CFG == 5
-constexpr int AS_WX = 1, AS_WY = 16, AS_PPT = 2;   // 32 x 32 region, 512 threads
-#else
-constexpr int AS_WX = 2, AS_WY = 8, AS_PPT = 2;    // 64 x 16 region, 512 threads
+#ifndef ADJ2_H
+#define ADJ2_H 32           // rows per warp
 #endif
+#ifndef ADJ2_D
+#define ADJ2_D 5            // ring slots
+#endif
+#ifndef ADJ2_MINB
+#define ADJ2_MINB 4
+#endif
+constexpr int ADJ2_OWN = 26;
 
-template <int TV, int CONS>
-static cudaError_t launch_adj_strip_t(const AdjParams& p, int batch, cudaStream_t s) {
-  constexpr int RW = 32 * AS_WX, RH = AS_PPT * AS_WY;
-  constexpr size_t smem = (size_t)RW * RH * 2 * sizeof(float2) + (size_t)AS_WY * RW * sizeof(float2);
-  dim3 grid((p.n + RW - 5) / (RW - 4), (p.m + RH - 5) / (RH - 4), batch);
-  adj_strip_kernel<TV, AS_WX, AS_WY, AS_PPT, CONS><<<grid, 32 * AS_WX * AS_WY, smem, s>>>(p);
-  return cudaGetLastError();
+struct Adj2Slot {
+  float4 R[32], RL[32], Y[32], N[32];
+  float2 B[32], BB[32];
+};
+
+__device__ __forceinline__ void adj2_issue(const AdjParams& p, Adj2Slot* sl, int lane, int gj, bool colin, bool own,
+                                          int j0, int j1, long long col) {
+  const bool in = colin && (unsigned)gj < (unsigned)p.m;
+  const long long o = in ? col + (long long)gj * p.n : 0;
+  const int s16 = in ? 16 : 0, s8 = in ? 8 : 0;
+  if (p.r != nullptr) cp_async16(&sl->R[lane], p.r + o, s16);
+  if (p.r_lo != nullptr) cp_async16(&sl->RL[lane], p.r_lo + o, s16);
+  cp_async8(&sl->B[lane], p.b + o, s8);
+  if (p.Y != nullptr) cp_async16(&sl->Y[lane], p.Y + o, s16);
+  if (p.rbn != nullptr) cp_async16(&sl->N[lane], p.rbn + o, s16);
+  const bool bo = own && gj >= j0 && gj < j1;
+  cp_async8(&sl->BB[lane], p.bbar + (bo ? o : 0), bo ? 8 : 0);
+  cp_async_commit();
 }
 
-template <int TV>
-static cudaError_t launch_adj_strip_tv(int cons, const AdjParams& p, int batch, cudaStream_t s) {
-  switch (cons) {
-    case CONS_NONE: return launch_adj_strip_t<TV, CONS_NONE>(p, batch, s);
-    case CONS_AMP: return launch_adj_strip_t<TV, CONS_AMP>(p, batch, s);
-    case CONS_RECT: return launch_adj_strip_t<TV, CONS_RECT>(p, batch, s);
-    default: return launch_adj_strip_t<TV, CONS_GEN>(p, batch, s);
+template <int TV, int CONS, bool EDGE>
+__device__ __forceinline__ float adj2_band(const AdjParams& p, Adj2Slot* ring, int lane, int gk, int j0, int j1,
+                                           long long col, float lam, float c8) {
+  const int n = p.n;
+  const bool colin = !EDGE || (unsigned)gk < (unsigned)n;
+  const bool own = colin && lane >= 3 && lane < 3 + ADJ2_OWN;
+  const bool kin = gk >= p.C.k0 && gk < p.C.k1;
+  const bool has_right = !EDGE || gk < n - 1;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  const float2 z2 = make_float2(0.f, 0.f);
+  AdjsState U, Lo;
+  adjs_init(p, p.r, U, colin, EDGE, j0 - 1, col);     // step k: first arriving row j0-2
+  adjs_init(p, p.r_lo, Lo, colin, EDGE, j0, col);     // step k-1: first arriving row j0-1
+  const int base = j0 - 2;   // row of slot 0
+#pragma unroll
+  for (int t = 0; t < ADJ2_D - 3; ++t) adj2_issue(p, ring + t, lane, base + t, colin, own, j0, j1, col);
+  float2 acc1 = z2, acc2 = z2;   // dL/db + what_k of rows i-2 and i-3
+  int slot = 0;                  // slot of row i
+  for (int i = base; i <= j1 + 3; ++i) {
+    // refill the slot of row i-3 (read for the last time last iteration) with row i-3+D
+    const int fill = slot >= 3 ? slot - 3 : slot + ADJ2_D - 3;
+    if (i - 3 + ADJ2_D <= j1 + 3) adj2_issue(p, ring + fill, lane, i - 3 + ADJ2_D, colin, own, j0, j1, col);
+    else cp_async_commit();
+    cp_async_wait<ADJ2_D - 3>();
+    const int s1 = slot >= 1 ? slot - 1 : slot + ADJ2_D - 1;
+    const int s2 = slot >= 2 ? slot - 2 : slot + ADJ2_D - 2;
+    // step k on row i
+    const Adj2Slot* sl = ring + slot;
+    const float4 R = p.r != nullptr ? sl->R[lane] : z4;
+    float4 Q = z4;
+    if (p.Y != nullptr) {
+      const float4 y = sl->Y[lane];
+      Q = q_scale(p.yc, y);
+    }
+    if (p.rbn != nullptr) {
+      const float4 y = sl->N[lane];
+      Q = q_axpy(p.rc, y, Q);
+    }
+    const int im = i - 1;
+    float2 whU;
+    float4 rbU;
+    adjs_core<TV, CONS, EDGE>(p, U, i, R, sl->B[lane], Q, colin, own && im >= j0 && im < j1, kin, has_right, gk,
+                              lam, c8, whU, rbU);
+    const int i2 = i - 2;
+    if (own && i2 >= j0 && i2 < j1) p.rb_out[col + (long long)i2 * n] = rbU;
+    const float2 bo = ring[s1].BB[lane];   // dL/db of row i-1 before this pass
+    const float2 acc0 = add_rn(bo, whU);
+    // step k-1 on row i-2
+    if (i >= j0 + 1) {
+      const Adj2Slot* sl2 = ring + s2;
+      const float4 RL = p.r_lo != nullptr ? sl2->RL[lane] : z4;
+      // same operation order as the single step's yc Y + rc rbar_{k+1}, so that
+      // pairing steps changes no bit of the result
+      float4 QL = z4;
+      if (p.rbn != nullptr) {
+        const float4 y = sl2->N[lane];
+        QL = q_scale(p.yc_lo, y);
+      }
+      QL = q_axpy(p.rc_lo, rbU, QL);
+      const int i3 = i - 3, i4 = i - 4;
+      float2 whL;
+      float4 rbL;
+      adjs_core<TV, CONS, EDGE>(p, Lo, i2, RL, sl2->B[lane], QL, colin, own && i3 >= j0 && i3 < j1, kin, has_right,
+                                gk, lam, c8, whL, rbL);
+      if (own && i3 >= j0 && i3 < j1) p.bbar[col + (long long)i3 * n] = add_rn(acc2, whL);
+      if (own && i4 >= j0 && i4 < j1) p.rb_out_lo[col + (long long)i4 * n] = rbL;
+    }
+    acc2 = acc1;
+    acc1 = acc0;
+    slot = slot == ADJ2_D - 1 ? 0 : slot + 1;
   }
+  cp_async_wait<0>();
+  return U.lacc + Lo.lacc;
+}
+
+template <int TV, int CONS>
+__global__ void __launch_bounds__(32 * ADJS_WARPS, ADJ2_MINB) adj2_stream_kernel(AdjParams p) {
+  const int lane = threadIdx.x & 31;
+  const int wc = blockIdx.x * ADJS_WARPS + (threadIdx.x >> 5);
+  const int m = p.m, n = p.n;
+  if (wc * ADJ2_OWN >= n) return;   // whole warp past the last column
+  const int z = blockIdx.z;
+  const float lam = fmaxf(p.lam_dev[z], 0.f);
+  const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
+  const int gk0 = wc * ADJ2_OWN - 3;
+  const int gk = gk0 + lane;
+  const int j0 = blockIdx.y * ADJ2_H;
+  const int j1 = min(j0 + ADJ2_H, m);
+  const long long col = (long long)z * p.px + gk;
+  const bool inside = gk0 >= 0 && gk0 + 32 <= n - 1 && j0 - 3 >= 0 && j1 + 4 <= m - 1;
+  extern __shared__ Adj2Slot adj2_ring[];
+  Adj2Slot* ring = adj2_ring + (threadIdx.x >> 5) * ADJ2_D;
+  const float lacc = inside ? adj2_band<TV, CONS, false>(p, ring, lane, gk, j0, j1, col, lam, c8)
+                            : adj2_band<TV, CONS, true>(p, ring, lane, gk, j0, j1, col, lam, c8);
+  double v = (double)lacc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) atomicAdd(p.lamacc + z, v);
 }
 
 template <int TV, int CONS>
 static cudaError_t launch_adj_stream_t(const AdjParams& p, int batch, cudaStream_t s) {
   const int ncw = (p.n + ADJS_OWN - 1) / ADJS_OWN;
   dim3 grid((ncw + ADJS_WARPS - 1) / ADJS_WARPS, (p.m + ADJS_H - 1) / ADJS_H, batch);
-#if CTV_ADJ_ASYNC
   constexpr size_t smem = sizeof(AdjsSlot) * ADJS_D * ADJS_WARPS;
   static bool attr_done = false;
   if (!attr_done) {
@@ -809,9 +710,6 @@ static cudaError_t launch_adj_stream_t(const AdjParams& p, int batch, cudaStream
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-#else
-  constexpr size_t smem = 0;
-#endif
   adj_stream_kernel<TV, CONS><<<grid, 32 * ADJS_WARPS, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -826,27 +724,51 @@ static cudaError_t launch_adj_stream_tv(int cons, const AdjParams& p, int batch,
   }
 }
 
-#ifndef CTV_ADJ_STREAM
-#define CTV_ADJ_STREAM 1
-#endif
+template <int TV, int CONS>
+static cudaError_t launch_adj2_t(const AdjParams& p, int batch, cudaStream_t s) {
+  const int ncw = (p.n + ADJ2_OWN - 1) / ADJ2_OWN;
+  dim3 grid((ncw + ADJS_WARPS - 1) / ADJS_WARPS, (p.m + ADJ2_H - 1) / ADJ2_H, batch);
+  constexpr size_t smem = sizeof(Adj2Slot) * ADJ2_D * ADJS_WARPS;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(adj2_stream_kernel<TV, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  adj2_stream_kernel<TV, CONS><<<grid, 32 * ADJS_WARPS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TV>
+static cudaError_t launch_adj2_tv(int cons, const AdjParams& p, int batch, cudaStream_t s) {
+  switch (cons) {
+    case CONS_NONE: return launch_adj2_t<TV, CONS_NONE>(p, batch, s);
+    case CONS_AMP: return launch_adj2_t<TV, CONS_AMP>(p, batch, s);
+    case CONS_RECT: return launch_adj2_t<TV, CONS_RECT>(p, batch, s);
+    default: return launch_adj2_t<TV, CONS_GEN>(p, batch, s);
+  }
+}
+
+// steps k and k-1 in one pass (p.r_lo, p.yc_lo, p.rc_lo, p.rb_out_lo set)
+static cudaError_t launch_adj_pair(int tv, const AdjParams& p, int batch, cudaStream_t s) {
+  const int cons = cons_mode(p.C);
+  switch (tv) {
+    case TV1_ISO: return launch_adj2_tv<TV1_ISO>(cons, p, batch, s);
+    case TV1_ANISO: return launch_adj2_tv<TV1_ANISO>(cons, p, batch, s);
+    case TV2_ISO: return launch_adj2_tv<TV2_ISO>(cons, p, batch, s);
+    default: return launch_adj2_tv<TV2_ANISO>(cons, p, batch, s);
+  }
+}
 
 static cudaError_t launch_adj_step(int tv, const AdjParams& p, int batch, cudaStream_t s) {
   const int cons = cons_mode(p.C);
-#if CTV_ADJ_STREAM
   switch (tv) {
     case TV1_ISO: return launch_adj_stream_tv<TV1_ISO>(cons, p, batch, s);
     case TV1_ANISO: return launch_adj_stream_tv<TV1_ANISO>(cons, p, batch, s);
     case TV2_ISO: return launch_adj_stream_tv<TV2_ISO>(cons, p, batch, s);
     default: return launch_adj_stream_tv<TV2_ANISO>(cons, p, batch, s);
   }
-#else
-  switch (tv) {
-    case TV1_ISO: return launch_adj_strip_tv<TV1_ISO>(cons, p, batch, s);
-    case TV1_ANISO: return launch_adj_strip_tv<TV1_ANISO>(cons, p, batch, s);
-    case TV2_ISO: return launch_adj_strip_tv<TV2_ISO>(cons, p, batch, s);
-    default: return launch_adj_strip_tv<TV2_ANISO>(cons, p, batch, s);
-  }
-#endif
 }
 
 static cudaError_t launch_adj_final(int tv, const AdjParams& p, int batch, cudaStream_t s) {
@@ -874,7 +796,7 @@ struct UnrolledLayout {
   float4* setq[2];
   float4* setr[2];
   float4* hist;                    // ckpt planes: r_k of the segment being walked back
-  float4* rb[3];
+  float4* rb[4];                   // rbar carries of the reverse walk
   size_t bytes;
 };
 
@@ -898,7 +820,7 @@ static UnrolledLayout layout(char* base, int batch, int m, int n, int K, int ckp
     L.setr[i] = (float4*)(base + off); off += plane;
   }
   L.hist = (float4*)(base + off); off += (size_t)ckpt * plane;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     L.rb[i] = (float4*)(base + off); off += plane;
   }
   L.bytes = off;
@@ -1102,24 +1024,42 @@ int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* la
       first = false;
       kk += steps;
     }
-    for (int k = k1; k >= k0 + 1; --k) {
-      const float4* rk;
-      if (k == k0 + 1) rk = sg == 0 ? nullptr : L.ckr[(size_t)sg];
-      else rk = L.hist + (long long)(k - k0 - 2) * plane;
+    auto r_of = [&](int k) -> const float4* {
+      if (k == k0 + 1) return sg == 0 ? nullptr : L.ckr[(size_t)sg];
+      return L.hist + (long long)(k - k0 - 2) * plane;
+    };
+    for (int k = k1; k >= k0 + 1;) {
       int oi = 0;
       while (oi == yi || oi == nbi) ++oi;
-      ap.r = rk;
+      ap.r = r_of(k);
       ap.Y = yi >= 0 ? L.rb[yi] : nullptr;
       ap.yc = yc;
       ap.rbn = nbi >= 0 ? L.rb[nbi] : nullptr;
       ap.rc = (float)(1.0 + beta[(size_t)k]);
       ap.rb_out = L.rb[oi];
+      if (CTV_ADJ_PAIR && k - 1 >= k0 + 1) {
+        // steps k and k-1 in one pass; the carries of step k-2 are rbar_k and rbar_{k-1}
+        int oj = 0;
+        while (oj == yi || oj == nbi || oj == oi) ++oj;
+        ap.r_lo = r_of(k - 1);
+        ap.yc_lo = (float)(-beta[(size_t)k]);
+        ap.rc_lo = (float)(1.0 + beta[(size_t)k - 1]);
+        ap.rb_out_lo = L.rb[oj];
+        if (launch_adj_pair(tv_type, ap, batch, s) != cudaSuccess) return CTV_ECUDA;
+        count_launch();
+        yi = oi;
+        yc = (float)(-beta[(size_t)k - 1]);
+        nbi = oj;
+        k -= 2;
+        continue;
+      }
       if (launch_adj_step(tv_type, ap, batch, s) != cudaSuccess) return CTV_ECUDA;
       count_launch();
       // next step k-1: carry = -beta_k rbar_{k+1}, and rbar_k just written
       yi = nbi;
       yc = (float)(-beta[(size_t)k]);
       nbi = oi;
+      --k;
     }
   }
   lambar_finish_kernel<<<(batch + 127) / 128, 128, 0, s>>>(L.lamacc, lambdabar, batch);

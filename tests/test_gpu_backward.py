@@ -77,7 +77,13 @@ def test_checkpoint_spacing_does_not_change_result(ckpt):
     ref = None
     _, gb, gl = gpu_grads(imgs, [0.05], 10, "tv1_iso", 0.5, ctv.Constraint(amp_max=1.0), xbar, ckpt)
     _, gb1, gl1 = gpu_grads(imgs, [0.05], 10, "tv1_iso", 0.5, ctv.Constraint(amp_max=1.0), xbar, 10)
-    assert np.array_equal(gb, gb1) and np.array_equal(gl, gl1)
+    # The spacing decides which reverse-step kernel runs (two steps per pass where
+    # a segment has two left, else one); the two are compiled separately, so the
+    # compiler may fuse a multiply and an add in one and not in the other, and
+    # the FP32 partial sums of dL/dlambda group pixels differently: equal up to
+    # FP32 rounding, not bit for bit.
+    np.testing.assert_allclose(gb, gb1, rtol=0, atol=1e-5 * np.abs(gb1).max())
+    np.testing.assert_allclose(gl, gl1, rtol=1e-5)
 
 
 def test_unrolled_forward_equals_batched_denoise():
