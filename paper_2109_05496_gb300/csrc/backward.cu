@@ -237,7 +237,7 @@ __global__ void lambar_finish_kernel(const double* acc, float* out, int batch) {
 // ---------------------------------------------------------------------------
 // Recompute pass that also stores r after every iteration (HIST tiles)
 // ---------------------------------------------------------------------------
-template <int KIND, int TV, int T, int A, int B, int C>
+template <int KIND, int TV, int T, int A, int B, int C, int CONS>
 __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kernel(PassParams p, float4* hist,
                                                                                 long long hist_plane) {
   using G = CfgGeom<KIND, A, B, C>;
@@ -247,8 +247,8 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
   I.ld = p.ld;
   I.q_in = p.q_in + z * p.d_stride;
   I.r_in = p.r_in + z * p.d_stride;
-  I.q_out = p.q_out + z * p.d_stride;
-  I.r_out = p.r_out + z * p.d_stride;
+  I.q_out = p.q_out != nullptr ? p.q_out + z * p.d_stride : nullptr;
+  I.r_out = p.r_out != nullptr ? p.r_out + z * p.d_stride : nullptr;
   I.m = p.m;
   I.n = p.n;
   const float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
   I.C = p.C;
   I.r_hist = hist + z * p.d_stride;
   I.hist_plane = hist_plane;
-  run_tile<KIND, TV, T, A, B, C, true>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
-                                       p.nsteps, p.first != 0);
+  run_tile<KIND, TV, T, A, B, C, true, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
+                                             p.nsteps, p.first != 0);
 }
 
 // configurations available to the recompute (a subset of the pass table)
@@ -266,21 +266,35 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
   X(2, 0, 4, 64, 32, 256)   \
   X(3, 1, 4, 2, 4, 8)       \
   X(5, 1, 6, 2, 8, 8)       \
-  X(11, 1, 4, 2, 8, 4)      \
   X(14, 1, 6, 2, 16, 4)
 
-template <int KIND, int TV, int T, int A, int B, int C>
-static cudaError_t launch_hist_t(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
+template <int KIND, int TV, int T, int A, int B, int C, int CONS>
+static cudaError_t launch_hist_c(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
   using G = CfgGeom<KIND, A, B, C>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_hist_pass_kernel<KIND, TV, T, A, B, C>,
+    cudaError_t e = cudaFuncSetAttribute(fgp_hist_pass_kernel<KIND, TV, T, A, B, C, CONS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  fgp_hist_pass_kernel<KIND, TV, T, A, B, C><<<grid, G::NT, G::SMEM, s>>>(p, hist, plane);
+  fgp_hist_pass_kernel<KIND, TV, T, A, B, C, CONS><<<grid, G::NT, G::SMEM, s>>>(p, hist, plane);
   return cudaGetLastError();
+}
+
+// P_C specialised per constraint kind, as in the forward pass (the region tile has one form)
+template <int KIND, int TV, int T, int A, int B, int C>
+static cudaError_t launch_hist_t(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
+  if constexpr (KIND == 0) {
+    return launch_hist_c<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, hist, plane, s);
+  } else {
+    switch (cons_mode(p.C)) {
+      case CONS_NONE: return launch_hist_c<KIND, TV, T, A, B, C, CONS_NONE>(p, grid, hist, plane, s);
+      case CONS_AMP: return launch_hist_c<KIND, TV, T, A, B, C, CONS_AMP>(p, grid, hist, plane, s);
+      case CONS_RECT: return launch_hist_c<KIND, TV, T, A, B, C, CONS_RECT>(p, grid, hist, plane, s);
+      default: return launch_hist_c<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, hist, plane, s);
+    }
+  }
 }
 
 template <int TV>
@@ -1013,8 +1027,10 @@ int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* la
       p.first = first ? 1 : 0;
       p.q_in = qin;
       p.r_in = rin;
-      p.q_out = L.setq[out];
-      p.r_out = L.setr[out];
+      // the last recompute pass of a segment keeps only its r_k history
+      const bool last = kk + steps > k1 - 1;
+      p.q_out = last ? nullptr : L.setq[out];
+      p.r_out = last ? nullptr : L.setr[out];
       if (launch_hist(tv_type, cfg, p, grid, L.hist + (long long)(kk - k0 - 1) * plane, plane, s) != cudaSuccess)
         return CTV_ECUDA;
       count_launch();

@@ -240,7 +240,7 @@ __device__ __forceinline__ void fgp_tile(const Img& I, int j0, int k0, const flo
     const int i = tid + s * NT;
     const int lj = i / RW, lk = i % RW;
     const int gj = gj0 + lj, gk = gk0 + lk;
-    if (lj >= T && lj < RH - T && lk >= T && lk < RW - T &&
+    if ((!HIST || I.q_out != nullptr) && lj >= T && lj < RH - T && lk >= T && lk < RW - T &&
         (unsigned)gj < (unsigned)I.m && (unsigned)gk < (unsigned)I.n) {
       const long long o = (long long)gj * I.n + gk;
       I.q_out[o] = qreg[s];
@@ -399,7 +399,8 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
     __syncthreads();
   }
 
-  if (lk >= T && lk < RW - T && colin) {
+  // (a recompute pass whose final state nobody reads passes q_out = nullptr)
+  if ((!HIST || I.q_out != nullptr) && lk >= T && lk < RW - T && colin) {
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
       const int lj = lj0 + s, gj = gj0 + s;
