@@ -180,7 +180,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--workload", default="denoise2048",
-                    choices=("denoise2048", "denoise256", "batched", "pr", "backward", "pr_paper"),
+                    choices=("denoise2048", "denoise2048_stop", "denoise256", "batched", "pr", "backward",
+                             "pr_paper"),
                     help="denoise2048 is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -304,6 +305,13 @@ def main():
         cpu = {"value": pxit / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d oracle solves of a %dx%d crop of the step images, 200 iterations each, "
                          "TV type cycling, FP64 PyTorch CPU" % (s, args.cpu_crop, args.cpu_crop)}
+        # the same oracle on one host thread
+        nt = torch.get_num_threads()
+        torch.set_num_threads(1)
+        a, b_, _ = oracle_sample(imgs_np, rect, 0, 128)
+        torch.set_num_threads(nt)
+        cpu["single_thread_value"] = a / b_ / 1e9
+        cpu["single_thread_sample"] = "one oracle solve of a 128x128 crop, 200 iterations, TV1 iso, 1 thread"
 
     clocks = sampler.summary()
     if rank == 0:
@@ -461,12 +469,67 @@ def run_other_workload(args, world, rank, local):
         ph0 = np.angle(x0.cpu().numpy() * np.conj(x_gt))
         ph0 = np.angle(np.exp(1j * (ph0 - np.angle(np.exp(1j * ph0).mean()))))
         h = hist.cpu().numpy()
+        # where the time goes: the fused FGP passes (timed per launch in a second, profiled run) and one
+        # gradient evaluation (two 2048^2 FFT pairs, the fused residual and the adjoint crop) per outer iteration
+        import ctypes
+        from paper_2109_05496_gb300 import _lib
+        lib = _lib.load()
+        lib.ctv_profile_enable(1)
+        plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
+        pass_ms, pass_n, units, all_n = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
+        lib.ctv_profile_read(ctypes.byref(pass_ms), ctypes.byref(pass_n), ctypes.byref(units), ctypes.byref(all_n))
+        lib.ctv_profile_enable(0)
+        reps = 50
+        g0, g1 = _events()
+        g0.record()
+        for _ in range(reps):
+            plan.gradient(x0, sqrt_y, Hg)
+        g1.record()
+        torch.cuda.synchronize()
+        grad_ms = g0.elapsed_time(g1) / reps
         out.update({"metric": "phase retrieval outer iterations/s (1024^2 object, 2048^2 FFTs, 10 FGP iterations each)",
                     "value": outer / (ms * 1e-3), "unit": "outer-iter/s", "higher_is_better": True,
                     "ms_total": ms, "fgp_pixel_iters": outer * 10 * m * n,
+                    "fgp_pass_ms_total": pass_ms.value, "fgp_pass_gpx_it_s": units.value / (pass_ms.value * 1e-3) / 1e9
+                    if pass_ms.value > 0 else None,
+                    "gradient_ms_per_outer": grad_ms, "gradient_share": grad_ms * outer / ms,
+                    "fgp_pass_share": pass_ms.value / ms,
                     "loss_first": float(h[0]), "loss_last": float(h[-1]),
                     "phase_rmse_initial": float(np.sqrt((ph0 ** 2).mean())),
                     "phase_rmse_final": float(np.sqrt((ph ** 2).mean()))})
+    elif args.workload == "denoise2048_stop":
+        # the 36 solves of the headline workload with the duality-gap test on (checked every 10 iterations,
+        # stop at gap <= 1e-6 P, at most 200 iterations): iterations to stop and time per solve
+        imgs_np, rect = make_inputs(0)
+        hm, hn = imgs_np[0].shape
+        C = ctv.Constraint(amp_max=1.0, rect=rect)
+        ws = ctv.workspace(1, hm, hn, dev)
+        x = torch.empty(hm, hn, dtype=torch.complex64, device=dev)
+        solves, tot_ms, tot_pxit = [], 0.0, 0.0
+        for ci, (sigma, lam) in enumerate(combos()):
+            b = torch.from_numpy(imgs_np[ci]).to(dev)
+            for tv in TVS:
+                opts = ctv.make_opts(ITERS, 10, 1e-6, 0.5, False, args.config)
+                st = ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws, want_stats=True)
+                torch.cuda.synchronize()
+                e0, e1 = _events()
+                e0.record()
+                for _ in range(args.steps):
+                    ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / args.steps
+                solves.append({"sigma": sigma, "lambda": lam, "tv": tv, "k_stop": st["iters"],
+                               "stopped": st["stopped"], "gap_rel": st["gap"] / max(st["primal"], 1e-30),
+                               "ms": t})
+                tot_ms += t
+                tot_pxit += st["iters"] * hm * hn
+        ks = [r["k_stop"] for r in solves]
+        out.update({"metric": "2048^2 solves with duality-gap stopping (gap <= 1e-6 P, checked every 10)",
+                    "value": tot_ms / len(solves), "unit": "ms/solve", "higher_is_better": False,
+                    "k_stop_mean": float(np.mean(ks)), "k_stop_min": int(min(ks)), "k_stop_max": int(max(ks)),
+                    "stopped_before_200": int(sum(1 for r in solves if r["stopped"])),
+                    "gpx_it_s_effective": tot_pxit / (tot_ms * 1e-3) / 1e9, "solves": solves})
     elif args.workload == "pr_paper":
         # the paper's simulated setting (Sec. VI-A): 256^2 pure phase object (phase in [0, pi]),
         # angular spectrum at 500 nm, 5 um pixels, 5 mm, 10% Gaussian intensity noise, back-propagated

@@ -137,7 +137,11 @@ static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct ctv_pr_plan {
   int m, n, M, N;
-  cufftHandle fft;
+  // The 2-D transforms of the M x N field run as 1-D passes: row transforms
+  // of only the m rows that hold the object (the others are zero on input,
+  // or not needed on output), and column transforms of every column.
+  cufftHandle fft_rows;   // m rows of length N, contiguous
+  cufftHandle fft_cols;   // N columns of length M, stride N
   char* base;        // one device allocation holding every buffer below
   size_t bytes;
   float2* P;         // M x N, zero outside the m x n corner, holds z
@@ -155,20 +159,47 @@ struct ctv_pr_plan {
 
 namespace ctv {
 
+static ctv_status pr_set_stream(ctv_pr_plan* p, cudaStream_t s) {
+  if (cufftSetStream(p->fft_rows, s) != CUFFT_SUCCESS || cufftSetStream(p->fft_cols, s) != CUFFT_SUCCESS)
+    return CTV_ECUDA;
+  return CTV_OK;
+}
+
+// F = FFT2(src) for a field that is zero outside its first m rows.
+static ctv_status pr_fft_padded(ctv_pr_plan* p, const float2* src, cudaStream_t s) {
+  if (p->M > p->m &&
+      cudaMemsetAsync(p->F + (size_t)p->m * p->N, 0, (size_t)(p->M - p->m) * p->N * sizeof(float2), s) != cudaSuccess)
+    return CTV_ECUDA;
+  if (cufftExecC2C(p->fft_rows, (cufftComplex*)src, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS)
+    return CTV_ECUDA;
+  if (cufftExecC2C(p->fft_cols, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS)
+    return CTV_ECUDA;
+  return CTV_OK;
+}
+
+// F = IFFT2(F) (unnormalised) on its first m rows; the other rows are left undefined.
+static ctv_status pr_ifft_rows(ctv_pr_plan* p) {
+  if (cufftExecC2C(p->fft_cols, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_INVERSE) != CUFFT_SUCCESS)
+    return CTV_ECUDA;
+  if (cufftExecC2C(p->fft_rows, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_INVERSE) != CUFFT_SUCCESS)
+    return CTV_ECUDA;
+  return CTV_OK;
+}
+
 // F(z) for the padded field src (object in its corner): FFT, H, IFFT, then the
 // residual g = (xi/|xi|)(|xi| - sqrt(y)) into Q's corner and 1/2 sum (|xi| - sqrt(y))^2.
 static ctv_status pr_forward_loss(ctv_pr_plan* p, const float2* src, const float* sqrt_y, const float2* H,
                                   double* loss_acc, cudaStream_t s) {
   const long long MN = (long long)p->M * p->N;
   const float inv = 1.0f / (float)MN;
-  if (cufftExecC2C(p->fft, (cufftComplex*)src, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_fft_padded(p, src, s) != CTV_OK) return CTV_ECUDA;
   if ((MN & 1) == 0) {
     pr_mul_h<<<152 * 8, 256, 0, s>>>((float4*)p->F, (const float4*)H, MN / 2, 0);
   } else {
     pr_mul_h_scalar<<<152 * 8, 256, 0, s>>>(p->F, H, MN, 0);
   }
   count_launch();
-  if (cufftExecC2C(p->fft, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_INVERSE) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_ifft_rows(p) != CTV_OK) return CTV_ECUDA;
   dim3 g((p->n + PR_NT - 1) / PR_NT, p->m);
   pr_residual<<<g, PR_NT, 0, s>>>(p->F, p->N, p->m, p->n, inv, sqrt_y, p->n, p->Q, p->N, loss_acc);
   count_launch();
@@ -178,14 +209,14 @@ static ctv_status pr_forward_loss(ctv_pr_plan* p, const float2* src, const float
 // A^* of the residual held in Q: FFT, conj(H), IFFT; grad F = (1/(MN)) F's corner.
 static ctv_status pr_adjoint(ctv_pr_plan* p, const float2* H, cudaStream_t s) {
   const long long MN = (long long)p->M * p->N;
-  if (cufftExecC2C(p->fft, (cufftComplex*)p->Q, (cufftComplex*)p->F, CUFFT_FORWARD) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_fft_padded(p, p->Q, s) != CTV_OK) return CTV_ECUDA;
   if ((MN & 1) == 0) {
     pr_mul_h<<<152 * 8, 256, 0, s>>>((float4*)p->F, (const float4*)H, MN / 2, 1);
   } else {
     pr_mul_h_scalar<<<152 * 8, 256, 0, s>>>(p->F, H, MN, 1);
   }
   count_launch();
-  if (cufftExecC2C(p->fft, (cufftComplex*)p->F, (cufftComplex*)p->F, CUFFT_INVERSE) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_ifft_rows(p) != CTV_OK) return CTV_ECUDA;
   return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
 }
 
@@ -228,14 +259,26 @@ int ctv_pr_plan_create(int m, int n, int M, int N, ctv_pr_plan** out) {
   p->dual_keep = (float4*)c; c += dual;
   p->loss = (double*)c;
   if (cudaMemset(p->base, 0, p->bytes) != cudaSuccess) { cudaFree(p->base); delete p; return CTV_ECUDA; }
-  if (cufftPlan2d(&p->fft, M, N, CUFFT_C2C) != CUFFT_SUCCESS) { cudaFree(p->base); delete p; return CTV_ENOMEM; }
+  int nr = N, nc = M;
+  if (cufftPlanMany(&p->fft_rows, 1, &nr, nullptr, 1, N, nullptr, 1, N, CUFFT_C2C, m) != CUFFT_SUCCESS) {
+    cudaFree(p->base);
+    delete p;
+    return CTV_ENOMEM;
+  }
+  if (cufftPlanMany(&p->fft_cols, 1, &nc, &nc, N, 1, &nc, N, 1, CUFFT_C2C, N) != CUFFT_SUCCESS) {
+    cufftDestroy(p->fft_rows);
+    cudaFree(p->base);
+    delete p;
+    return CTV_ENOMEM;
+  }
   *out = p;
   return CTV_OK;
 }
 
 void ctv_pr_plan_destroy(ctv_pr_plan* p) {
   if (p == nullptr) return;
-  cufftDestroy(p->fft);
+  cufftDestroy(p->fft_rows);
+  cufftDestroy(p->fft_cols);
   cudaFree(p->base);
   delete p;
 }
@@ -246,7 +289,7 @@ int ctv_pr_gradient(ctv_pr_plan* p, const void* z, const float* sqrt_y, const vo
   if (p == nullptr || z == nullptr || sqrt_y == nullptr || H == nullptr || grad == nullptr) return CTV_EINVAL;
   if (((uintptr_t)H & 15) || ((uintptr_t)z & 7) || ((uintptr_t)grad & 7)) return CTV_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_set_stream(p, s) != CTV_OK) return CTV_ECUDA;
   dim3 g((p->n + 255) / 256, p->m);
   pr_copy<<<g, 256, 0, s>>>((const float2*)z, p->n, p->P, p->N, p->m, p->n);
   count_launch();
@@ -268,7 +311,7 @@ int ctv_pr_solve(ctv_pr_plan* p, const float* sqrt_y, const void* H, float tau, 
   if (!(tau >= 0.f) || !(gamma > 0.f) || isinf(tau) || isinf(gamma) || outer_iters < 0) return CTV_EINVAL;
   if (tv_type < 0 || tv_type > 3) return CTV_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_set_stream(p, s) != CTV_OK) return CTV_ECUDA;
   const int m = p->m, n = p->n;
   dim3 g((n + 255) / 256, m);
   // z_1 = x_0 (into the padded buffer), x_{0} kept as the first "previous" iterate
@@ -323,7 +366,7 @@ int ctv_pr_solve_ls(ctv_pr_plan* p, const float* sqrt_y, const void* H, float ta
     return CTV_EINVAL;
   if (tv_type < 0 || tv_type > 3) return CTV_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return CTV_ECUDA;
+  if (pr_set_stream(p, s) != CTV_OK) return CTV_ECUDA;
   const int m = p->m, n = p->n;
   dim3 g((n + 255) / 256, m);
   dim3 gr((n + PR_NT - 1) / PR_NT, m);
