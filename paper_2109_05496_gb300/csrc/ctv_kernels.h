@@ -56,6 +56,8 @@ struct GapParams {
 };
 
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s);
+// Streaming multiprocessors of the current device (queried once).
+int sm_count();
 // Per-TV-type launchers, instantiated one translation unit per type (pass_tv*.cu).
 template <int TV>
 cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);

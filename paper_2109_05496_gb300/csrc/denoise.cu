@@ -52,9 +52,17 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
   g.lam = bad_lam ? 0.f : lam;
   g.alpha = p.alpha;
   g.C = p.C;
-  double acc[3];
-  gap_tile<TV>(g, blockIdx.y * (GAP_RH - 2), blockIdx.x * (GAP_RW - 2), qs, xs, red, acc);
-  gap_commit(st, acc, gridDim.x * gridDim.y, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+  // blocks loop over the image's tiles (few blocks, so that a launch after the
+  // stop costs little and the FP64 atomics stay few)
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int tx = (p.n + GAP_RW - 3) / (GAP_RW - 2), ty = (p.m + GAP_RH - 3) / (GAP_RH - 2);
+  for (int t = blockIdx.x; t < tx * ty; t += gridDim.x) {
+    const int by = t / tx, bx = t - by * tx;
+    gap_tile_add<TV>(g, by * (GAP_RH - 2), bx * (GAP_RW - 2), qs, xs, acc);
+    __syncthreads();
+  }
+  block_sum<GAP_NT, 3>(acc, red);
+  gap_commit(st, acc, gridDim.x, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
 }
 
 // ----------------------------------------------------------------------------
@@ -122,8 +130,40 @@ cudaError_t launch_finalize(const GapParams& p, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int TV>
+static int gap_blocks(const GapParams& p) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_gap_kernel<TV>, GAP_NT, 0) != cudaSuccess ||
+        per_sm <= 0)
+      per_sm = 1;
+  }
+  const long long tiles = (long long)((p.n + GAP_RW - 3) / (GAP_RW - 2)) * ((p.m + GAP_RH - 3) / (GAP_RH - 2));
+  const long long cap = (long long)per_sm * sm_count();
+  return (int)(tiles < cap ? tiles : cap);
+}
+
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
-  dim3 grid((p.n + GAP_RW - 3) / (GAP_RW - 2), (p.m + GAP_RH - 3) / (GAP_RH - 2), batch);
+  int nb = 1;
+  switch (tv) {
+    case TV1_ISO: nb = gap_blocks<TV1_ISO>(p); break;
+    case TV1_ANISO: nb = gap_blocks<TV1_ANISO>(p); break;
+    case TV2_ISO: nb = gap_blocks<TV2_ISO>(p); break;
+    case TV2_ANISO: nb = gap_blocks<TV2_ANISO>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  dim3 grid(nb, 1, batch);
   switch (tv) {
     case TV1_ISO: fgp_gap_kernel<TV1_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
     case TV1_ANISO: fgp_gap_kernel<TV1_ANISO><<<grid, GAP_NT, 0, s>>>(p); break;

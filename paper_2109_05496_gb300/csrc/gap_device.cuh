@@ -28,9 +28,11 @@ constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
 // needs x below and to the right. Returns, in thread 0, the block's sums of
 //   acc[0] = ||x - b||^2, acc[1] = TV(x), acc[2] = ||b||^2 - ||w||^2 + ||w - P_C(w)||^2
 // (w = b - lam L^T q), i.e. 2 P - 2 lam TV and 2 D of App. A.
+// gap_tile_add adds this thread's share of the three sums into acc (no block
+// reduction; the caller synchronises before reusing qs and xs).
 template <int TV>
-__device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4* qs, float2* xs, double* red,
-                                         double (&acc)[3]) {
+__device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, float4* qs, float2* xs,
+                                             double (&acc)[3]) {
   constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
   const int m = g.m, n = g.n;
   const int gj0 = j0 - 1, gk0 = k0 - 1;
@@ -91,10 +93,17 @@ __device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4
       if (g.q_export != nullptr) g.q_export[(long long)gj * n + gk] = qc;
     }
   }
-  acc[0] = (double)fa0;
-  acc[1] = (double)fa1;
-  acc[2] = (double)fa2;
-  block_sum<NT, 3>(acc, red);
+  acc[0] += (double)fa0;
+  acc[1] += (double)fa1;
+  acc[2] += (double)fa2;
+}
+
+template <int TV>
+__device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4* qs, float2* xs, double* red,
+                                         double (&acc)[3]) {
+  acc[0] = acc[1] = acc[2] = 0.0;
+  gap_tile_add<TV>(g, j0, k0, qs, xs, acc);
+  block_sum<GAP_NT, 3>(acc, red);
 }
 
 // Adds the block sums into st and lets the last block of the reduction turn them
