@@ -454,8 +454,10 @@ def run_other_workload(args, world, rank, local):
         x0.copy_(-g)                    # A^* sqrt(y): the gradient at 0 is -A^*(sqrt(y))
         outer = 300
         C = ctv.Constraint(amp_max=1.0)
+        # warm-up: full solves, long enough for the clocks to settle (a few ms of work left the
+        # timed solve at a fraction of the steady rate)
         for _ in range(args.warmup):
-            plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, 10)
+            plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
         torch.cuda.synchronize()
         e0, e1 = _events()
         e0.record()
