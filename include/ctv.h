@@ -157,6 +157,13 @@ int ctv_autotune_denoise(const void* b, void* x, int m, int n, int ld, float lam
  * -------------------------------------------------------------------------- */
 size_t ctv_denoise_workspace_size(int batch, int m, int n);
 
+/* Solves that can stop early (check_every > 0 and gap_tol > 0, at least two
+ * check intervals, batch * m * n >= 512 * 512) are, from the second call with
+ * identical arguments on, run as a cached CUDA graph whose check intervals are
+ * conditional nodes, so that the intervals after the stop cost nothing; such a
+ * call is still asynchronous on `stream`. Calls on a stream that is being
+ * captured, and calls while ctv_profile_enable(1) is in force, always launch
+ * their passes directly. */
 int ctv_denoise(const void* b, void* x, int m, int n, int ld, float lambda,
                 const ctv_constraint* C, int tv_type, const ctv_opts* opts,
                 void* dual_state, void* workspace, size_t workspace_bytes,

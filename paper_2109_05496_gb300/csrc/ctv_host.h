@@ -28,6 +28,7 @@ struct DenoiseCall {
   size_t workspace_bytes;
   ctv_stats* stats;
   ctv_stream stream;
+  int plain_launches;   // nonzero: never build a stop graph (callers that must not allocate)
 };
 
 ctv_status run_denoise(const DenoiseCall& c);
@@ -42,6 +43,9 @@ bool config_info(int i, int* T, int* RW, int* RH, int* NT);
 
 // Measurement hooks (prof.cu): count every launch; time fused passes when enabled.
 void count_launch();
+void count_launches(int n);
+// whether ctv_profile_enable(1) is in force (pass launches are then bracketed by events)
+bool prof_active();
 int prof_begin(cudaStream_t s);
 void prof_end(int slot, cudaStream_t s, double units);
 

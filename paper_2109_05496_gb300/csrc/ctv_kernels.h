@@ -30,6 +30,9 @@ struct PassParams {
   int first;
 };
 
+// Check intervals a stop graph can hold (solves with more run as plain launches).
+#define CTV_MAX_STOP_INTERVALS 64
+
 // One launch of the finalize / gap evaluation over an equally sized batch.
 struct GapParams {
   const float2* b;
@@ -53,6 +56,10 @@ struct GapParams {
   int iter;
   double gap_tol;
   int final_call;
+  // inside a stop graph: the handles of the later check intervals, cleared when
+  // the test passes (a conditional handle belongs to one conditional node)
+  int n_cond;
+  cudaGraphConditionalHandle cond[CTV_MAX_STOP_INTERVALS];
 };
 
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s);

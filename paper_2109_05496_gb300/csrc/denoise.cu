@@ -14,6 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "ctv.h"
@@ -63,6 +66,9 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
   }
   block_sum<GAP_NT, 3>(acc, red);
   gap_commit(st, acc, gridDim.x, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+  // inside a stop graph, the check that stops the solve skips the remaining intervals
+  if (p.n_cond > 0 && threadIdx.x == 0 && last && st->stop)
+    for (int i = 0; i < p.n_cond; ++i) cudaGraphSetConditional(p.cond[i], 0u);
 }
 
 // ----------------------------------------------------------------------------
@@ -250,6 +256,169 @@ void nesterov_betas(int K, std::vector<double>* beta) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// Stop graphs. A solve with gap checks and a tolerance launches every pass up
+// front; once the test passes, the device flag turns the remaining passes into
+// launches that return at once, but each still costs its block launches (about
+// 15 us per pass at 2048^2). On large images such a solve instead runs as a CUDA
+// graph in which each check interval (its passes and its check) is the body of
+// a conditional IF node with its own handle (a handle belongs to one node): the
+// check whose test passes clears the handles of all later intervals
+// (cudaGraphSetConditional) and the graph skips them. The handles' default value
+// (1) is restored at every launch, so an instantiated graph is reused by later
+// calls with identical arguments; it is built on the second such call, since
+// building it costs more host time than one solve saves.
+// ----------------------------------------------------------------------------
+constexpr double kStopGraphMinPixels = 512.0 * 512.0;
+
+struct StopGraph {
+  cudaGraph_t G = nullptr;
+  std::vector<cudaGraphConditionalHandle> h;   // one per check interval
+  int next = 0;                                 // interval opened next
+  cudaStream_t cs = nullptr;          // private stream the bodies are captured on
+  cudaGraphNode_t prev = nullptr;     // last node of the chain
+  cudaGraph_t fin = nullptr;          // the finalize, added as a child graph
+  bool have_prev = false, open = false;
+  int kernels = 0;
+
+  bool begin(int intervals) {
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
+    h.assign((size_t)intervals, 0);
+    for (int i = 0; i < intervals; ++i)
+      if (cudaGraphConditionalHandleCreate(&h[(size_t)i], G, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return false;
+    return cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  }
+  // the handles a check at the end of the interval just opened must clear
+  void later_handles(GapParams* g) const {
+    g->n_cond = 0;
+    for (size_t i = (size_t)next; i < h.size(); ++i) g->cond[g->n_cond++] = h[i];
+  }
+  // appends an IF node after the chain and starts capturing its body
+  cudaStream_t open_interval() {
+    if (next >= (int)h.size()) return nullptr;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    memset(&np.conditional, 0, sizeof(np.conditional));
+    np.conditional.handle = h[(size_t)next++];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, G, have_prev ? &prev : nullptr, nullptr, have_prev ? 1 : 0, &np) != cudaSuccess)
+      return nullptr;
+    if (cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return nullptr;
+    prev = node;
+    have_prev = true;
+    open = true;
+    return cs;
+  }
+  bool close_interval() {
+    cudaGraph_t body;
+    open = false;
+    return cudaStreamEndCapture(cs, &body) == cudaSuccess;
+  }
+  cudaStream_t open_final() {
+    if (cudaGraphCreate(&fin, 0) != cudaSuccess) return nullptr;
+    if (cudaStreamBeginCaptureToGraph(cs, fin, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return nullptr;
+    open = true;
+    return cs;
+  }
+  bool close_final() {
+    cudaGraph_t g2;
+    open = false;
+    if (cudaStreamEndCapture(cs, &g2) != cudaSuccess) return false;
+    cudaGraphNode_t node;
+    return cudaGraphAddChildGraphNode(&node, G, have_prev ? &prev : nullptr, have_prev ? 1 : 0, fin) == cudaSuccess;
+  }
+  cudaGraphExec_t instantiate() {
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, G, 0) != cudaSuccess) return nullptr;
+    return ex;
+  }
+  ~StopGraph() {
+    if (open && cs != nullptr) {
+      cudaGraph_t g2 = nullptr;
+      cudaStreamEndCapture(cs, &g2);
+    }
+    if (fin != nullptr) cudaGraphDestroy(fin);
+    if (G != nullptr) cudaGraphDestroy(G);
+    if (cs != nullptr) cudaStreamDestroy(cs);
+  }
+};
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return true;
+  return cst != cudaStreamCaptureStatusNone;
+}
+
+// every argument that shapes the launches, as bytes
+static std::string stop_graph_key(const DenoiseCall& c, const ConsDev& C, int cfg) {
+  std::string k;
+  auto add = [&k](const void* p, size_t n) { k.append((const char*)p, n); };
+  int dev = -1;
+  cudaGetDevice(&dev);
+  add(&dev, sizeof(dev));
+  add(&c.b, sizeof(c.b));
+  add(&c.x, sizeof(c.x));
+  add(&c.batch, sizeof(c.batch));
+  add(&c.batch_stride, sizeof(c.batch_stride));
+  add(&c.m, sizeof(c.m));
+  add(&c.n, sizeof(c.n));
+  add(&c.ld, sizeof(c.ld));
+  add(&c.lam, sizeof(c.lam));
+  add(&c.lam_dev, sizeof(c.lam_dev));
+  add(&c.tv, sizeof(c.tv));
+  add(&c.dual_state, sizeof(c.dual_state));
+  add(&c.workspace, sizeof(c.workspace));
+  add(c.opts, sizeof(ctv_opts));
+  add(&C, sizeof(C));
+  add(&cfg, sizeof(cfg));
+  return k;
+}
+
+static std::mutex g_sg_mu;
+static std::vector<std::pair<std::string, std::pair<cudaGraphExec_t, int>>> g_sg_cache;   // most recent last
+constexpr size_t kStopGraphCache = 16;
+
+// Keys of solves seen once: instantiating a stop graph costs more host time than
+// one solve saves, so a graph is built on the second call with the same arguments.
+static std::vector<std::string> g_sg_seen;
+
+static bool stop_graph_seen_before(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_sg_mu);
+  for (size_t i = 0; i < g_sg_seen.size(); ++i)
+    if (g_sg_seen[i] == key) return true;
+  if (g_sg_seen.size() >= 4 * kStopGraphCache) g_sg_seen.erase(g_sg_seen.begin());
+  g_sg_seen.push_back(key);
+  return false;
+}
+
+static cudaGraphExec_t stop_graph_lookup(const std::string& key, int* kernels) {
+  std::lock_guard<std::mutex> lk(g_sg_mu);
+  for (size_t i = 0; i < g_sg_cache.size(); ++i) {
+    if (g_sg_cache[i].first == key) {
+      auto e = g_sg_cache[i];
+      g_sg_cache.erase(g_sg_cache.begin() + (long)i);
+      g_sg_cache.push_back(e);
+      *kernels = e.second.second;
+      return e.second.first;
+    }
+  }
+  return nullptr;
+}
+
+static void stop_graph_store(const std::string& key, cudaGraphExec_t ex, int kernels) {
+  std::lock_guard<std::mutex> lk(g_sg_mu);
+  if (g_sg_cache.size() >= kStopGraphCache) {
+    cudaGraphExecDestroy(g_sg_cache.front().second.first);   // freed once any launch of it completes
+    g_sg_cache.erase(g_sg_cache.begin());
+  }
+  g_sg_cache.push_back({key, {ex, kernels}});
+}
+
 ctv_status run_denoise(const DenoiseCall& c) {
   if (c.b == nullptr || c.x == nullptr || c.workspace == nullptr) return CTV_EINVAL;
   if (c.batch <= 0 || c.m <= 0 || c.n <= 0 || c.ld < c.n) return CTV_EINVAL;
@@ -308,88 +477,148 @@ ctv_status run_denoise(const DenoiseCall& c) {
   g.st = st;
   g.gap_tol = gap_tol;
 
-  int last_set = -1;   // -1: no pass has run
-  if (K > 0 && !lam_zero) {
-    std::vector<double> beta;
-    nesterov_betas(K, &beta);
-    if (o != nullptr && o->plain_gp) std::fill(beta.begin(), beta.end(), 0.0);   // Eq. (21): r_{k+1} = q_k
-    PassParams p;
-    memset(&p, 0, sizeof(p));
-    p.b = (const float2*)c.b;
-    p.b_stride = c.batch_stride;
-    p.ld = c.ld;
-    p.d_stride = (long long)px;
-    p.m = c.m;
-    p.n = c.n;
-    p.lam = c.lam;
-    p.lam_dev = c.lam_dev;
-    p.alpha = alpha;
-    p.C = C;
-    p.st = st;
-    const dim3 grid = pass_grid(cfg, c.m, c.n, c.batch);
-    if (grid.y > 65535) return CTV_EINVAL;
-    int k = 1;
-    int out = 0;
-    const float4* q_in = (const float4*)c.dual_state;
-    const float4* r_in = (const float4*)c.dual_state;
-    bool first = !warm;
-    while (k <= K) {
-      int steps = K - k + 1;
-      if (steps > cf.T) steps = cf.T;
-      if (check_every > 0) {
-        const int to_check = check_every - ((k - 1) % check_every);
-        if (steps > to_check) steps = to_check;
-      }
-      for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
-      p.nsteps = steps;
-      p.first = first ? 1 : 0;
-      p.q_in = q_in;
-      p.r_in = r_in;
-      p.q_out = set_q[out];
-      p.r_out = set_r[out];
-      const int slot = prof_begin(s);
-      if (launch_pass(c.tv, cfg, p, grid, s) != cudaSuccess) return CTV_ECUDA;
-      count_launch();
-      prof_end(slot, s, (double)c.batch * (double)px * (double)steps);
-      first = false;
-      k += steps;
-      last_set = out;
-      q_in = set_q[out];
-      r_in = set_r[out];
-      out ^= 1;
-      if (check_every > 0 && (k - 1) % check_every == 0 && k - 1 < K) {
-        g.default_set = last_set;
-        g.zero_q = 0;
-        g.x = nullptr;
-        g.q_export = nullptr;
-        g.iter = k - 1;
-        g.final_call = 0;
-        if (launch_gap(c.tv, g, c.batch, s) != cudaSuccess) return CTV_ECUDA;
+  // the passes, checks and finalize of the solve, onto stream es, or (sg != nullptr) into a
+  // stop graph whose check intervals are conditional nodes
+  auto enqueue = [&](cudaStream_t es, StopGraph* sg) -> ctv_status {
+    GapParams gg = g;
+    int last_set = -1;   // -1: no pass has run
+    if (K > 0 && !lam_zero) {
+      std::vector<double> beta;
+      nesterov_betas(K, &beta);
+      if (o != nullptr && o->plain_gp) std::fill(beta.begin(), beta.end(), 0.0);   // Eq. (21): r_{k+1} = q_k
+      PassParams p;
+      memset(&p, 0, sizeof(p));
+      p.b = (const float2*)c.b;
+      p.b_stride = c.batch_stride;
+      p.ld = c.ld;
+      p.d_stride = (long long)px;
+      p.m = c.m;
+      p.n = c.n;
+      p.lam = c.lam;
+      p.lam_dev = c.lam_dev;
+      p.alpha = alpha;
+      p.C = C;
+      p.st = st;
+      const dim3 grid = pass_grid(cfg, c.m, c.n, c.batch);
+      if (grid.y > 65535) return CTV_EINVAL;
+      int k = 1;
+      int out = 0;
+      const float4* q_in = (const float4*)c.dual_state;
+      const float4* r_in = (const float4*)c.dual_state;
+      bool first = !warm;
+      while (k <= K) {
+        if (sg != nullptr && !sg->open) {
+          es = sg->open_interval();
+          if (es == nullptr) return CTV_ECUDA;
+        }
+        int steps = K - k + 1;
+        if (steps > cf.T) steps = cf.T;
+        if (check_every > 0) {
+          const int to_check = check_every - ((k - 1) % check_every);
+          if (steps > to_check) steps = to_check;
+        }
+        for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
+        p.nsteps = steps;
+        p.first = first ? 1 : 0;
+        p.q_in = q_in;
+        p.r_in = r_in;
+        p.q_out = set_q[out];
+        p.r_out = set_r[out];
+        const int slot = sg == nullptr ? prof_begin(es) : -1;
+        if (launch_pass(c.tv, cfg, p, grid, es) != cudaSuccess) return CTV_ECUDA;
         count_launch();
+        if (sg != nullptr) sg->kernels++;
+        prof_end(slot, es, (double)c.batch * (double)px * (double)steps);
+        first = false;
+        k += steps;
+        last_set = out;
+        q_in = set_q[out];
+        r_in = set_r[out];
+        out ^= 1;
+        if (check_every > 0 && (k - 1) % check_every == 0 && k - 1 < K) {
+          gg.default_set = last_set;
+          gg.zero_q = 0;
+          gg.x = nullptr;
+          gg.q_export = nullptr;
+          gg.iter = k - 1;
+          gg.final_call = 0;
+          if (sg != nullptr) sg->later_handles(&gg);
+          else gg.n_cond = 0;
+          if (launch_gap(c.tv, gg, c.batch, es) != cudaSuccess) return CTV_ECUDA;
+          count_launch();
+          if (sg != nullptr) {
+            sg->kernels++;
+            if (!sg->close_interval()) return CTV_ECUDA;
+          }
+        }
       }
+      if (sg != nullptr && sg->open && !sg->close_interval()) return CTV_ECUDA;
+    }
+    // finalize: x = P_C(b - lam L^T q_K), final statistics, optional export of q_K
+    if (sg != nullptr) {
+      es = sg->open_final();
+      if (es == nullptr) return CTV_ECUDA;
+    }
+    gg.x = (float2*)c.x;
+    gg.x_stride = c.batch_stride;
+    gg.q_export = (float4*)c.dual_state;
+    gg.final_call = 1;
+    gg.n_cond = 0;
+    gg.iter = (K > 0 && !lam_zero) ? K : 0;
+    if (last_set >= 0) {
+      gg.default_set = last_set;
+      gg.zero_q = 0;
+    } else if (warm) {
+      gg.default_set = 2;   // the warm-start dual itself
+      gg.zero_q = lam_zero ? 1 : 0;
+    } else {
+      gg.default_set = 0;
+      gg.zero_q = 1;
+    }
+    if (warm && last_set < 0 && gg.q_export == gg.dual_in) gg.q_export = nullptr;  // unchanged
+    // without gap checks and with nobody reading the statistics, only x (and q) are written
+    const bool light = c.stats == nullptr && check_every == 0;
+    if ((light ? launch_finalize(gg, c.batch, es) : launch_gap(c.tv, gg, c.batch, es)) != cudaSuccess)
+      return CTV_ECUDA;
+    count_launch();
+    if (sg != nullptr) {
+      sg->kernels++;
+      if (!sg->close_final()) return CTV_ECUDA;
+    }
+    return CTV_OK;
+  };
+
+  // Solves that can stop early run, on large images, as a cached CUDA graph whose
+  // check intervals are conditional nodes (see StopGraph); otherwise, and if the
+  // graph cannot be built, the launches go straight onto the stream.
+  bool done = false;
+  if (!c.plain_launches && K > check_every && check_every > 0 && gap_tol > 0.0 && !lam_zero &&
+      (K + check_every - 1) / check_every <= CTV_MAX_STOP_INTERVALS &&
+      (double)c.batch * (double)px >= kStopGraphMinPixels && !prof_active() && !stream_capturing(s)) {
+    std::string key = stop_graph_key(c, C, cfg);
+    int kernels = 0;
+    cudaGraphExec_t ex = stop_graph_lookup(key, &kernels);
+    const bool hit = ex != nullptr;
+    if (ex == nullptr && stop_graph_seen_before(key)) {
+      StopGraph sg;
+      if (sg.begin((K + check_every - 1) / check_every)) {
+        const ctv_status est = enqueue(nullptr, &sg);
+        if (est == CTV_OK) ex = sg.instantiate();
+        kernels = sg.kernels;
+        if (ex != nullptr) stop_graph_store(key, ex, kernels);
+      }
+      cudaGetLastError();   // a failed build falls back to plain launches
+    }
+    if (ex != nullptr) {
+      if (cudaGraphLaunch(ex, s) != cudaSuccess) return CTV_ECUDA;
+      if (hit) count_launches(kernels);   // a new graph counted its kernels as it was built
+      done = true;
     }
   }
-  // finalize: x = P_C(b - lam L^T q_K), final statistics, optional export of q_K
-  g.x = (float2*)c.x;
-  g.x_stride = c.batch_stride;
-  g.q_export = (float4*)c.dual_state;
-  g.final_call = 1;
-  g.iter = (K > 0 && !lam_zero) ? K : 0;
-  if (last_set >= 0) {
-    g.default_set = last_set;
-    g.zero_q = 0;
-  } else if (warm) {
-    g.default_set = 2;   // the warm-start dual itself
-    g.zero_q = lam_zero ? 1 : 0;
-  } else {
-    g.default_set = 0;
-    g.zero_q = 1;
+  if (!done) {
+    const ctv_status est = enqueue(s, nullptr);
+    if (est != CTV_OK) return est;
   }
-  if (warm && last_set < 0 && g.q_export == g.dual_in) g.q_export = nullptr;  // unchanged
-  // without gap checks and with nobody reading the statistics, only x (and q) are written
-  const bool light = c.stats == nullptr && check_every == 0;
-  if ((light ? launch_finalize(g, c.batch, s) : launch_gap(c.tv, g, c.batch, s)) != cudaSuccess) return CTV_ECUDA;
-  count_launch();
 
   if (c.stats != nullptr) {
     std::vector<DevStats> hs((size_t)c.batch);

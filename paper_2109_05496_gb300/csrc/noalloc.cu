@@ -80,6 +80,7 @@ int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lamb
   c.workspace_bytes = kNoAllocScratchBytes;
   c.stats = stats;
   c.stream = stream;
+  c.plain_launches = 1;   // a stop graph would allocate driver resources when instantiated
   return ctv::run_denoise(c);
 }
 

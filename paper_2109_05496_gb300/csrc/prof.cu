@@ -26,6 +26,11 @@ long long g_launch_base = 0;
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool prof_active() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
 
 int prof_begin(cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);

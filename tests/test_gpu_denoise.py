@@ -289,3 +289,105 @@ def test_plain_gradient_projection(tv):
     b, res = run_oracle(noisy, 0.05, 40, tv, 0.5, Co, accelerate=False)
     check_parity(x, res, b, noisy, 0.05, tv, 0.5)
     assert st["iters"] == 40
+
+
+# --------------------------------------------------------------- finalize with and without statistics
+@pytest.mark.parametrize("tv", TV_NAMES)
+@pytest.mark.parametrize("kind", ["amp_rect", "none"])
+def test_light_finalize_matches_gap_finalize(tv, kind):
+    # Without gap checks and without statistics the solve ends with the finalize
+    # that writes only x (and q); with statistics it ends with the gap kernel.
+    # Both evaluate Eq. (18) the same way, so x and the exported q agree bit for bit.
+    m, n = 83, 131
+    _, noisy = noisy_phantom(m, n, 0.1, seed=31)
+    Cg, _ = cons_pair(kind, m, n)
+    b = torch.from_numpy(to_c64(noisy)).cuda()
+    x_light, x_stats = torch.empty_like(b), torch.empty_like(b)
+    d_light = torch.zeros(m * n * 4, dtype=torch.float32, device="cuda")
+    d_stats = torch.zeros_like(d_light)
+    opts = ctv.make_opts(23, 0, 0.0, 0.5)
+    ctv.ctv_denoise(b, x_light, 0.05, Cg, tv, opts, dual_state=d_light)
+    st = ctv.ctv_denoise(b, x_stats, 0.05, Cg, tv, opts, dual_state=d_stats, want_stats=True)
+    torch.cuda.synchronize()
+    assert st["iters"] == 23
+    assert torch.equal(x_light, x_stats)
+    assert torch.equal(d_light, d_stats)
+
+
+def test_light_finalize_row_stride():
+    # images that are column windows of wider buffers (row stride ld > n)
+    m, n, ld = 57, 70, 96
+    _, noisy = noisy_phantom(m, ld, 0.1, seed=32)
+    wide = torch.from_numpy(to_c64(noisy)).cuda()
+    b = wide[:, 3:3 + n]
+    out_a = torch.zeros_like(wide)
+    out_b = torch.zeros_like(wide)
+    opts = ctv.make_opts(17, 0, 0.0, 0.5)
+    C = ctv.Constraint(amp_max=1.0)
+    ctv.ctv_denoise(b, out_a[:, 3:3 + n], 0.04, C, "tv2_iso", opts)
+    ctv.ctv_denoise(b, out_b[:, 3:3 + n], 0.04, C, "tv2_iso", opts, want_stats=True)
+    ref = ctv.denoise(b.contiguous(), 0.04, "tv2_iso", 17, C, 0.5)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_b)
+    assert torch.equal(out_a[:, 3:3 + n], ref)
+    assert not out_a[:, :3].any() and not out_a[:, 3 + n:].any()   # nothing written outside the window
+
+
+# --------------------------------------------------------------- stop graphs (early-stopping solves on large images)
+@pytest.mark.parametrize("tv,tol", [("tv1_iso", 1e-4), ("tv2_aniso", 1e-4), ("tv1_aniso", 1e-12)])
+def test_stop_graph_matches_plain_launches(tv, tol):
+    # From 512^2 pixels on, a solve with gap checks and a tolerance runs as a CUDA
+    # graph whose check intervals are conditional nodes; with profiling on it
+    # launches its passes one by one instead. Same kernels, same order: the same
+    # x, the same stopping iteration. A call with new arguments launches plainly,
+    # the second identical call builds the graph, later ones reuse it.
+    from paper_2109_05496_gb300 import _lib
+    lib = _lib.load()
+    m, n = 520, 530
+    _, noisy = noisy_phantom(m, n, 0.1, seed=41)
+    Cg, _ = cons_pair("amp_rect", m, n)
+    b = torch.from_numpy(to_c64(noisy)).cuda()
+    x0 = torch.empty_like(b)
+    x = torch.empty_like(b)
+    opts = ctv.make_opts(200, 10, tol, 0.5)
+    lib.ctv_profile_enable(1)
+    try:
+        s0 = ctv.ctv_denoise(b, x0, 0.05, Cg, tv, opts, want_stats=True)
+    finally:
+        lib.ctv_profile_enable(0)
+    runs = []
+    for _ in range(3):   # plain (first sight), graph built, graph reused
+        x.fill_(0)
+        st = ctv.ctv_denoise(b, x, 0.05, Cg, tv, opts, want_stats=True)
+        torch.cuda.synchronize()
+        runs.append((st, x.clone()))
+    torch.cuda.synchronize()
+    if tol > 1e-6:
+        assert s0["stopped"] and 0 < s0["iters"] < 200
+    else:
+        assert not s0["stopped"] and s0["iters"] == 200
+    for s, xr in runs:
+        assert (s["iters"], s["stopped"]) == (s0["iters"], s0["stopped"])
+        assert s["primal"] == pytest.approx(s0["primal"], rel=1e-12)
+        assert s["gap"] == pytest.approx(s0["gap"], rel=1e-9, abs=1e-12 * s0["primal"])
+        assert torch.equal(xr, x0)
+
+
+def test_stop_graph_changed_arguments_rebuild():
+    # a different lambda or output buffer is a different graph, not a stale one
+    m, n = 512, 512
+    _, noisy = noisy_phantom(m, n, 0.1, seed=42)
+    b = torch.from_numpy(to_c64(noisy)).cuda()
+    C = ctv.Constraint(amp_max=1.0)
+    opts = ctv.make_opts(120, 10, 1e-5, 0.5)
+    outs = {}
+    for lam in (0.03, 0.03, 0.08, 0.08, 0.03):   # second sights build graphs; the last call reuses one
+        x = torch.empty_like(b)
+        st = ctv.ctv_denoise(b, x, lam, C, "tv1_iso", opts, want_stats=True)
+        torch.cuda.synchronize()
+        ref = ctv.denoise(b, lam, "tv1_iso", st["iters"], C, 0.5)   # plain solve of the same length
+        torch.cuda.synchronize()
+        assert torch.equal(x, ref)
+        outs.setdefault(lam, []).append((st["iters"], x))
+    for lam, rs in outs.items():
+        assert all(r[0] == rs[0][0] and torch.equal(r[1], rs[0][1]) for r in rs)
