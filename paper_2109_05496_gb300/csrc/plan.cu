@@ -214,8 +214,25 @@ struct ctv_plan {
 
 namespace ctv {
 
-static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
+// The schedule of one execution, captured on s. The passes of different TV types
+// touch different images, so each type's passes form their own chain (streams
+// aux[t], forked from s and joined back at every gap launch): in the graph the
+// four chains run concurrently and fill each other's launch tails.
+static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s, const cudaStream_t* aux, cudaEvent_t* ev) {
   if (cudaMemsetAsync(P->d_st, 0, sizeof(DevStats) * (size_t)P->count, s) != cudaSuccess) return CTV_ECUDA;
+  auto fork = [&]() -> bool {
+    if (cudaEventRecord(ev[4], s) != cudaSuccess) return false;
+    for (int t = 0; t < 4; ++t)
+      if (cudaStreamWaitEvent(aux[t], ev[4], 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() -> bool {
+    for (int t = 0; t < 4; ++t)
+      if (cudaEventRecord(ev[t], aux[t]) != cudaSuccess || cudaStreamWaitEvent(s, ev[t], 0) != cudaSuccess)
+        return false;
+    return true;
+  };
+  if (!fork()) return CTV_ECUDA;
   int launches = 0;
   int last_set = -1;
   int T = 1;
@@ -245,7 +262,7 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
         const int nb = P->tv_begin[t + 1] - P->tv_begin[t];
         if (nb == 0) continue;
         p.items = P->d_pass + P->tv_begin[t];
-        if (launch_list(t, P->cfg, P->cons, p, nb, s, false) != cudaSuccess) return CTV_ECUDA;
+        if (launch_list(t, P->cfg, P->cons, p, nb, aux[t], false) != cudaSuccess) return CTV_ECUDA;
         ++launches;
       }
       first = false;
@@ -257,9 +274,11 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
         g.zero_q = 0;
         g.iter = k - 1;
         g.final_call = 0;
+        if (!join()) return CTV_ECUDA;
         fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
         if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
         ++launches;
+        if (!fork()) return CTV_ECUDA;
       }
     }
   }
@@ -267,6 +286,7 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s) {
   g.zero_q = last_set < 0 ? 1 : 0;
   g.iter = K;
   g.final_call = 1;
+  if (!join()) return CTV_ECUDA;
   fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
   if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
   ++launches;
@@ -377,21 +397,35 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   memset(&dummy, 0, sizeof(dummy));
   for (int t = 0; t < 4; ++t) ok = ok && launch_list(t, cfg, cons, dummy, 0, nullptr, true) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) == cudaSuccess;
+  cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int t = 0; t < 4; ++t) ok = ok && cudaStreamCreateWithFlags(&aux[t], cudaStreamNonBlocking) == cudaSuccess;
+  for (int t = 0; t < 5; ++t) ok = ok && cudaEventCreateWithFlags(&ev[t], cudaEventDisableTiming) == cudaSuccess;
+  auto drop_aux = [&]() {
+    for (int t = 0; t < 4; ++t)
+      if (aux[t] != nullptr) cudaStreamDestroy(aux[t]);
+    for (int t = 0; t < 5; ++t)
+      if (ev[t] != nullptr) cudaEventDestroy(ev[t]);
+  };
   if (!ok) {
+    drop_aux();
+    if (P->cap != nullptr) cudaStreamDestroy(P->cap);
     cudaFree(P->dev);
     delete P;
     return CTV_ECUDA;
   }
   // capture the schedule once
   if (cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    drop_aux();
     cudaStreamDestroy(P->cap);
     cudaFree(P->dev);
     delete P;
     return CTV_ECUDA;
   }
-  ctv_status st = plan_enqueue(P, P->cap);
+  ctv_status st = plan_enqueue(P, P->cap, aux, ev);
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(P->cap, &graph);
+  drop_aux();
   if (st != CTV_OK || ce != cudaSuccess || graph == nullptr ||
       cudaGraphInstantiate(&P->exec, graph, 0) != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
