@@ -24,7 +24,9 @@
   X(11, 1, 4, 2, 8, 4)       \
   X(12, 1, 2, 2, 8, 4)       \
   X(13, 1, 4, 2, 16, 4)      \
-  X(14, 1, 6, 2, 16, 4)
+  X(14, 1, 6, 2, 16, 4)      \
+  X(15, 1, 4, 1, 16, 2)      \
+  X(16, 1, 4, 1, 32, 1)
 
 namespace ctv {
 

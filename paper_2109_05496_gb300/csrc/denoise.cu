@@ -193,12 +193,14 @@ int default_config(int m, int n, int iters, int tv) {
     const int t = tuned_config(m, n, tv);
     if (t >= 0) return t;
   }
-  // measured on GB300 (2048^2, 1024^2 and 256^2 phantoms, 200 iterations, all four
-  // TV types): column-strip kernels with 4 rows per thread (two 512-thread blocks
-  // per SM); 4 iterations per 64 x 32 region at 2048^2 and 256^2, 6 per 64 x 64
-  // region around 1024^2
+  // measured on GB300 (2048^2 to 256^2 phantoms, all four TV types): column-strip
+  // kernels; 4 iterations per 64 x 32 region, 4 rows per thread, two 512-thread
+  // blocks per SM at 2048^2; 6 per 64 x 64 region around 1024^2; below about
+  // 448^2, where too few regions fill the GPU, 4 per 32 x 32 region with one row
+  // per thread (1024 threads; 133 against 219 us for 100 iterations at 256^2)
   const double px = (double)m * (double)n;
-  if (m > 0 && n > 0 && px >= 512.0 * 512.0 && px < 1536.0 * 1536.0) return 14;
+  if (px < 448.0 * 448.0) return 16;
+  if (px < 1536.0 * 1536.0) return 14;
   return 11;
 }
 
