@@ -157,8 +157,8 @@ int ctv_autotune_denoise(const void* b, void* x, int m, int n, int ld, float lam
  * -------------------------------------------------------------------------- */
 size_t ctv_denoise_workspace_size(int batch, int m, int n);
 
-/* Solves that can stop early (check_every > 0 and gap_tol > 0, at least two
- * check intervals, batch * m * n >= 512 * 512) are, from the second call with
+/* Single-image solves that can stop early (check_every > 0 and gap_tol > 0,
+ * at least two check intervals, m * n >= 512 * 512) are, from the second call with
  * identical arguments on, run as a cached CUDA graph whose check intervals are
  * conditional nodes, so that the intervals after the stop cost nothing; such a
  * call is still asynchronous on `stream`. Calls on a stream that is being

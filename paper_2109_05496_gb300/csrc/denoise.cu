@@ -594,9 +594,11 @@ ctv_status run_denoise(const DenoiseCall& c) {
   // check intervals are conditional nodes (see StopGraph); otherwise, and if the
   // graph cannot be built, the launches go straight onto the stream.
   bool done = false;
-  if (!c.plain_launches && K > check_every && check_every > 0 && gap_tol > 0.0 && !lam_zero &&
-      (K + check_every - 1) / check_every <= CTV_MAX_STOP_INTERVALS &&
-      (double)c.batch * (double)px >= kStopGraphMinPixels && !prof_active() && !stream_capturing(s)) {
+  // (one image only: in a batch each image stops on its own, and a check clears the
+  // graph's handles for the whole launch)
+  if (!c.plain_launches && c.batch == 1 && K > check_every && check_every > 0 && gap_tol > 0.0 && !lam_zero &&
+      (K + check_every - 1) / check_every <= CTV_MAX_STOP_INTERVALS && (double)px >= kStopGraphMinPixels &&
+      !prof_active() && !stream_capturing(s)) {
     std::string key = stop_graph_key(c, C, cfg);
     int kernels = 0;
     cudaGraphExec_t ex = stop_graph_lookup(key, &kernels);

@@ -391,3 +391,24 @@ def test_stop_graph_changed_arguments_rebuild():
         outs.setdefault(lam, []).append((st["iters"], x))
     for lam, rs in outs.items():
         assert all(r[0] == rs[0][0] and torch.equal(r[1], rs[0][1]) for r in rs)
+
+
+def test_batched_stopping_is_per_image():
+    # A batch large enough for a stop graph if it were one image: each image must
+    # stop on its own check, whatever the others do.
+    B, m, n = 4, 260, 260
+    imgs = np.stack([to_c64(noisy_phantom(m, n, 0.1, seed=60 + i)[1]) for i in range(B)])
+    lams = torch.tensor([0.01, 0.1, 0.03, 0.06], dtype=torch.float32, device="cuda")
+    b = torch.from_numpy(imgs).cuda()
+    C = ctv.Constraint(amp_max=1.0)
+    opts = ctv.make_opts(150, 10, 1e-5, 0.5)
+    for _ in range(3):   # also after the library has seen the arguments before
+        x = torch.empty_like(b)
+        st = ctv.ctv_denoise_batched(b, x, lams, C, "tv1_iso", opts, want_stats=True)
+        torch.cuda.synchronize()
+        for i in range(B):
+            xi = torch.empty_like(b[i])
+            si = ctv.ctv_denoise(b[i], xi, float(lams[i]), C, "tv1_iso", opts, want_stats=True)
+            torch.cuda.synchronize()
+            assert st[i]["iters"] == si["iters"]
+            assert torch.equal(x[i], xi)
