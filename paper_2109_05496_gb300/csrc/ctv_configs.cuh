@@ -26,7 +26,8 @@
   X(13, 1, 4, 2, 16, 4)      \
   X(14, 1, 6, 2, 16, 4)      \
   X(15, 1, 4, 1, 16, 2)      \
-  X(16, 1, 4, 1, 32, 1)
+  X(16, 1, 4, 1, 32, 1)      \
+  X(17, 1, 8, 1, 32, 1)
 
 namespace ctv {
 

@@ -196,10 +196,12 @@ int default_config(int m, int n, int iters, int tv) {
   // measured on GB300 (2048^2 to 256^2 phantoms, all four TV types): column-strip
   // kernels; 4 iterations per 64 x 32 region, 4 rows per thread, two 512-thread
   // blocks per SM at 2048^2; 6 per 64 x 64 region around 1024^2; below about
-  // 448^2, where too few regions fill the GPU, 4 per 32 x 32 region with one row
-  // per thread (1024 threads; 133 against 219 us for 100 iterations at 256^2)
+  // 448^2, where too few regions fill the GPU, 32 x 32 regions with one row per
+  // thread (1024 threads) and 8 iterations per pass (15.5 against 10.5
+  // Gpixel-iter/s for 4 iterations at 128^2, 63 against 57 at 384^2; at 256^2
+  // the 4-iteration config 16 is 5% faster)
   const double px = (double)m * (double)n;
-  if (px < 448.0 * 448.0) return 16;
+  if (px < 448.0 * 448.0) return 17;
   if (px < 1536.0 * 1536.0) return 14;
   return 11;
 }
