@@ -209,7 +209,11 @@ int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lamb
  * Each image has its own shape, lambda, alpha, TV type and C; all share
  * opts->max_iters, check_every and gap_tol (warm_start must be 0; config -1
  * picks one; plans support configurations 2, 7, 11 and 14, others return
- * CTV_EUNSUPPORTED). ctv_plan_create copies the descriptors, allocates the plan's
+ * CTV_EUNSUPPORTED; CTV_CONFIG_AUTOTUNE makes ctv_plan_create build a plan in
+ * each supported configuration in turn, time one execution of it after a
+ * warm-up on the caller's images (writing their x, synchronising), and keep the fastest -
+ * the autotuning of tile and T for this batch; no counterpart in the paper).
+ * ctv_plan_create copies the descriptors, allocates the plan's
  * device memory (dual state 64 bytes per pixel plus work lists) and captures the
  * whole schedule - one launch per pass over the tiles of all images - into a
  * CUDA graph; ctv_plan_execute replays it on `stream` (asynchronous). The b and
@@ -225,6 +229,7 @@ typedef struct {
   ctv_constraint C;
 } ctv_image_desc;
 
+#define CTV_CONFIG_AUTOTUNE (-2)
 typedef struct ctv_plan ctv_plan;
 
 int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts, ctv_plan** out);

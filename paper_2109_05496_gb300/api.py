@@ -315,7 +315,11 @@ class Plan:
     same shape and row stride), lam, and optionally tv, alpha, C."""
 
     def __init__(self, images: Sequence[dict], iters: int, check_every: int = 0, gap_tol: float = 0.0,
-                 config: int = -1):
+                 config: Union[int, str] = -1):
+        # config: -1 the default, a plan configuration, or "auto" to time every plan
+        # configuration on these images and keep the fastest (CTV_CONFIG_AUTOTUNE)
+        if config == "auto":
+            config = -2
         self._lib = L.load()
         n = len(images)
         arr = (L.CtvImageDesc * n)()

@@ -305,6 +305,45 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   if (descs == nullptr || count <= 0 || opts == nullptr) return CTV_EINVAL;
   if (opts->max_iters < 0 || opts->check_every < 0 || !(opts->gap_tol >= 0.0) || opts->warm_start) return CTV_EINVAL;
   if (opts->plain_gp) return CTV_EUNSUPPORTED;
+  if (opts->config == CTV_CONFIG_AUTOTUNE) {
+    // time one execution of a plan in each supported configuration on these images
+    // (one candidate's memory at a time) and build the fastest
+    cudaStream_t ts;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) return CTV_ECUDA;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) { cudaStreamDestroy(ts); return CTV_ECUDA; }
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); cudaStreamDestroy(ts); return CTV_ECUDA; }
+    int best = -1;
+    float best_ms = 0.f;
+    ctv_status st = CTV_OK;
+    ctv_opts o = *opts;
+#define CTV_PLAN_TRY(id, kind, T, A, B, C)                                                    \
+    if (st == CTV_OK) {                                                                       \
+      o.config = id;                                                                          \
+      ctv_plan* cand = nullptr;                                                               \
+      st = (ctv_status)ctv_plan_create(descs, count, &o, &cand);                              \
+      if (st == CTV_OK) {                                                                     \
+        float ms = 0.f;                                                                       \
+        if (ctv_plan_execute(cand, (ctv_stream)ts) != CTV_OK || cudaEventRecord(e0, ts) != cudaSuccess || \
+            ctv_plan_execute(cand, (ctv_stream)ts) != CTV_OK || cudaEventRecord(e1, ts) != cudaSuccess || \
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) \
+          st = CTV_ECUDA;                                                                     \
+        else if (best < 0 || ms < best_ms) {                                                  \
+          best = id;                                                                          \
+          best_ms = ms;                                                                       \
+        }                                                                                     \
+        ctv_plan_destroy(cand);                                                               \
+      }                                                                                       \
+    }
+    CTV_PLAN_CONFIGS(CTV_PLAN_TRY)
+#undef CTV_PLAN_TRY
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(ts);
+    if (st != CTV_OK) return st;
+    o.config = best;
+    return ctv_plan_create(descs, count, &o, out);
+  }
   int cfg = opts->config;
   if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
   if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1);

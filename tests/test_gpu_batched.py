@@ -57,6 +57,24 @@ def test_plan_matches_oracle_and_loop(config):
         assert torch.equal(a, im["x"])
 
 
+def test_plan_autotune_picks_a_plan_configuration():
+    # config "auto": every plan configuration is timed on these images and the
+    # fastest kept; its results are those of a plan built with that configuration
+    shapes, lams, types, imgs = make_batch(10, 3, 180, seed=8)
+    ims = plan_images(imgs, lams, types)
+    plan = ctv.Plan(ims, 20, config="auto")
+    cfg = plan.info()["config"]
+    assert cfg in (2, 7, 11, 14)
+    plan.execute()
+    torch.cuda.synchronize()
+    got = [im["x"].clone() for im in ims]
+    ref = ctv.Plan(ims, 20, config=cfg)
+    ref.execute()
+    torch.cuda.synchronize()
+    for a, im in zip(got, ims):
+        assert torch.equal(a, im["x"])
+
+
 def test_plan_gap_stopping_per_image():
     shapes, lams, types, imgs = make_batch(8, 40, 120, seed=9)
     ims = plan_images(imgs, lams, types)
