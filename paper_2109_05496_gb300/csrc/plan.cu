@@ -53,6 +53,7 @@ struct ListPassParams {
   int out_set;
   int first;
   int nsteps;
+  int can_stop;   // the plan has gap checks: a block first tests its image's stop flag
   float beta[8];
 };
 
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kern
   using G = CfgGeom<KIND, A, B, C>;
   const WorkItem w = p.items[blockIdx.x];
   const PlanImg d = p.imgs[w.img];
-  if (*(volatile const int*)&d.st->stop) return;
+  if (p.can_stop && *(volatile const int*)&d.st->stop) return;
   Img I;
   I.b = d.b;
   I.ld = d.ld;
@@ -256,6 +257,7 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s, const cudaStream_t* 
       for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)P->beta[(size_t)k + i] : 0.f;
       p.nsteps = steps;
       p.first = first ? 1 : 0;
+      p.can_stop = every > 0 ? 1 : 0;
       p.in_set = out ^ 1;
       p.out_set = out;
       for (int t = 0; t < 4; ++t) {
