@@ -502,7 +502,9 @@ ctv_status run_denoise(const DenoiseCall& c) {
       p.lam_dev = c.lam_dev;
       p.alpha = alpha;
       p.C = C;
-      p.st = st;
+      // the stop flag is read by every block before its loads; without a stopping test
+      // nobody sets it, so the passes skip that read
+      p.st = check_every > 0 && gap_tol > 0.0 ? st : nullptr;
       const dim3 grid = pass_grid(cfg, c.m, c.n, c.batch);
       if (grid.y > 65535) return CTV_EINVAL;
       int k = 1;
