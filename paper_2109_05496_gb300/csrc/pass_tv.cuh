@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include "ctv_configs.cuh"
 #include "ctv_device.cuh"
@@ -11,9 +12,21 @@
 
 namespace ctv {
 
+#ifndef CTV_PDL
+#define CTV_PDL 1
+#endif
+
 template <int KIND, int TV, int T, int A, int B, int C, int CONS>
 __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(PassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
+#if CTV_PDL
+  // Programmatic dependent launch: the next pass may be scheduled onto SMs this
+  // grid's last wave leaves idle (launch_dependents), and this grid's blocks wait
+  // for the previous kernel's results before their first load (wait). Both are
+  // no-ops for a launch without the programmatic attribute.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
   const int z = blockIdx.z;
   if (p.st != nullptr && *(volatile const int*)&p.st[z].stop) return;
   Img I;
@@ -45,8 +58,23 @@ static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s)
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
+#if CTV_PDL
+  cudaLaunchConfig_t lc;
+  memset(&lc, 0, sizeof(lc));
+  lc.gridDim = grid;
+  lc.blockDim = dim3(G::NT);
+  lc.dynamicSmemBytes = G::SMEM;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>, p);
+#else
   fgp_pass_kernel<KIND, TV, T, A, B, C, CONS><<<grid, G::NT, G::SMEM, s>>>(p);
   return cudaGetLastError();
+#endif
 }
 
 // Region kernels (kind 0) use the general constraint path; column-strip kernels
