@@ -61,7 +61,9 @@ template <int KIND, int TV, int CONS, int T, int A, int B, int C>
 __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kernel(ListPassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
   const WorkItem w = p.items[blockIdx.x];
-  const PlanImg d = p.imgs[w.img];
+  // fields read from global memory one by one (a register copy of the
+  // descriptor indexed by the runtime set number would live in local memory)
+  const PlanImg& d = p.imgs[w.img];
   if (p.can_stop && *(volatile const int*)&d.st->stop) return;
   Img I;
   I.b = d.b;
@@ -78,7 +80,16 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kern
   I.r_hist = nullptr;
   I.hist_plane = 0;
   const int j0 = (w.tile / d.tiles_x) * (G::RH - 2 * T), k0 = (w.tile % d.tiles_x) * (G::RW - 2 * T);
-  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, j0, k0, p.beta, p.nsteps, p.first != 0);
+  // The extrapolation weights go through shared memory: indexing the parameter
+  // array by the runtime step number would copy the whole parameter block into
+  // local memory. The tile's first barrier (after its loads) orders these
+  // stores before the first use.
+  __shared__ float beta_s[8];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) beta_s[i] = p.beta[i];
+  }
+  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, j0, k0, beta_s, p.nsteps, p.first != 0);
 }
 
 struct ListGapParams {
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
   __shared__ double red[3 * (GAP_NT / 32)];
   __shared__ int last;
   const WorkItem w = p.items[blockIdx.x];
-  const PlanImg d = p.imgs[w.img];
+  const PlanImg& d = p.imgs[w.img];
   const int stopped = *(volatile int*)&d.st->stop;
   if (!p.final_call && stopped) return;
   const int set = stopped ? d.st->stop_set : p.default_set;
