@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
     __syncthreads();
   }
   block_sum<GAP_NT, 3>(acc, red);
-  gap_commit(st, acc, gridDim.x, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+  gap_commit(st, acc, gridDim.x, 1u, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
   // inside a stop graph, the check that stops the solve skips the remaining intervals
   if (p.n_cond > 0 && threadIdx.x == 0 && last && st->stop)
     for (int i = 0; i < p.n_cond; ++i) cudaGraphSetConditional(p.cond[i], 0u);

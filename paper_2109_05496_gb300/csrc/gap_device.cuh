@@ -106,17 +106,19 @@ __device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4
   block_sum<GAP_NT, 3>(acc, red);
 }
 
-// Adds the block sums into st and lets the last block of the reduction turn them
-// into primal, dual and gap, apply the stopping test (checks) or record the final
-// iteration count, and reset the accumulators. Thread 0 holds the block sums.
-__device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3], unsigned nblk, float lam, bool bad_lam,
-                                           int set, int stopped, int iter, double gap_tol, int final_call, int* last) {
+// Adds the block sums into st and lets the commit that completes the reduction
+// (nblk units in all; this one covers `units` of them) turn them into primal,
+// dual and gap, apply the stopping test (checks) or record the final iteration
+// count, and reset the accumulators. Thread 0 holds the block sums.
+__device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3], unsigned nblk, unsigned units,
+                                           float lam, bool bad_lam, int set, int stopped, int iter, double gap_tol,
+                                           int final_call, int* last) {
   if (threadIdx.x == 0) {
     atomicAdd(&st->acc[0], acc[0]);
     atomicAdd(&st->acc[1], acc[1]);
     atomicAdd(&st->acc[2], acc[2]);
     __threadfence();
-    *last = (atomicAdd(&st->blocks_done, 1u) == nblk - 1) ? 1 : 0;
+    *last = (atomicAdd(&st->blocks_done, units) + units == nblk) ? 1 : 0;
   }
   __syncthreads();
   if (*last && threadIdx.x == 0) {

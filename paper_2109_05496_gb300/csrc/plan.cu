@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kern
 struct ListGapParams {
   const PlanImg* imgs;
   const WorkItem* items;
+  int n_items;
   int default_set;
   int zero_q;
   int iter;
@@ -102,36 +103,79 @@ struct ListGapParams {
   int final_call;
 };
 
+__device__ __forceinline__ void list_gap_commit(const PlanImg* d, double (&acc)[3], double* red, unsigned units,
+                                                int set, int stopped, int iter, double gap_tol, int final_call,
+                                                int* last) {
+  block_sum<GAP_NT, 3>(acc, red);
+  gap_commit(d->st, acc, d->gnblk, units, d->lam, false, set, stopped, iter, gap_tol, final_call, last);
+  acc[0] = acc[1] = acc[2] = 0.0;
+}
+
+// Persistent: each block walks a contiguous run of gap tiles (items are in
+// image order, so a run covers one image or a few), keeps per-thread FP64 sums
+// while the image stays the same and commits them - one block reduction and one
+// set of atomics - when the image changes or the run ends. A commit counts the
+// tiles it covers, so an image's reduction completes with its last tile.
 __global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
   __shared__ float4 qs[GAP_RW * GAP_RH];
   __shared__ float2 xs[GAP_RW * GAP_RH];
   __shared__ double red[3 * (GAP_NT / 32)];
   __shared__ int last;
-  const WorkItem w = p.items[blockIdx.x];
-  const PlanImg& d = p.imgs[w.img];
-  const int stopped = *(volatile int*)&d.st->stop;
-  if (!p.final_call && stopped) return;
-  const int set = stopped ? d.st->stop_set : p.default_set;
-  GapImg g;
-  g.b = d.b;
-  g.ld = d.ld;
-  g.q = (p.zero_q && !stopped) ? nullptr : d.q[set];
-  g.x = p.final_call ? d.x : nullptr;
-  g.q_export = nullptr;
-  g.m = d.m;
-  g.n = d.n;
-  g.lam = d.lam;
-  g.alpha = d.alpha;
-  g.C = d.C;
-  const int j0 = (w.tile / d.gtiles_x) * (GAP_RH - 2), k0 = (w.tile % d.gtiles_x) * (GAP_RW - 2);
-  double acc[3];
-  switch (d.tv) {
-    case TV1_ISO: gap_tile<TV1_ISO>(g, j0, k0, qs, xs, red, acc); break;
-    case TV1_ANISO: gap_tile<TV1_ANISO>(g, j0, k0, qs, xs, red, acc); break;
-    case TV2_ISO: gap_tile<TV2_ISO>(g, j0, k0, qs, xs, red, acc); break;
-    default: gap_tile<TV2_ANISO>(g, j0, k0, qs, xs, red, acc); break;
+  const int per = (p.n_items + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int i0 = (int)blockIdx.x * per, i1 = min(i0 + per, p.n_items);
+  double acc[3] = {0.0, 0.0, 0.0};
+  int cur = -1, cur_set = 0, cur_stopped = 0;
+  unsigned units = 0;
+  for (int i = i0; i < i1; ++i) {
+    const WorkItem w = p.items[i];
+    if (w.img != cur && units > 0) {
+      list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last);
+      units = 0;
+    }
+    cur = w.img;
+    const PlanImg& d = p.imgs[w.img];
+    // (an image's stop flag cannot change while its tiles are being evaluated:
+    // it is set only by the commit that completes the image)
+    const int stopped = *(volatile int*)&d.st->stop;
+    if (!p.final_call && stopped) continue;
+    const int set = stopped ? d.st->stop_set : p.default_set;
+    cur_set = set;
+    cur_stopped = stopped;
+    GapImg g;
+    g.b = d.b;
+    g.ld = d.ld;
+    g.q = (p.zero_q && !stopped) ? nullptr : d.q[set];
+    g.x = p.final_call ? d.x : nullptr;
+    g.q_export = nullptr;
+    g.m = d.m;
+    g.n = d.n;
+    g.lam = d.lam;
+    g.alpha = d.alpha;
+    g.C = d.C;
+    const int j0 = (w.tile / d.gtiles_x) * (GAP_RH - 2), k0 = (w.tile % d.gtiles_x) * (GAP_RW - 2);
+    switch (d.tv) {
+      case TV1_ISO: gap_tile_add<TV1_ISO>(g, j0, k0, qs, xs, acc); break;
+      case TV1_ANISO: gap_tile_add<TV1_ANISO>(g, j0, k0, qs, xs, acc); break;
+      case TV2_ISO: gap_tile_add<TV2_ISO>(g, j0, k0, qs, xs, acc); break;
+      default: gap_tile_add<TV2_ANISO>(g, j0, k0, qs, xs, acc); break;
+    }
+    __syncthreads();   // qs and xs are reused by the next tile
+    ++units;
   }
-  gap_commit(d.st, acc, d.gnblk, d.lam, false, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+  if (units > 0)
+    list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last);
+}
+
+// Blocks of a gap / finalize launch: resident blocks, at most one per item.
+static int gap_list_blocks(int n_items) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_gap_list_kernel, GAP_NT, 0) != cudaSuccess ||
+        per_sm <= 0)
+      per_sm = 1;
+  }
+  const long long cap = (long long)per_sm * sm_count();
+  return (int)(n_items < cap ? n_items : cap);
 }
 
 template <int KIND, int TV, int CONS, int T, int A, int B, int C>
@@ -254,6 +298,8 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s, const cudaStream_t* 
   memset(&g, 0, sizeof(g));
   g.imgs = P->d_imgs;
   g.items = P->d_gap;
+  g.n_items = P->n_gap;
+  const int gap_grid = gap_list_blocks(P->n_gap);
   g.gap_tol = P->gap_tol;
   if (K > 0) {
     ListPassParams p;
@@ -288,7 +334,7 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s, const cudaStream_t* 
         g.iter = k - 1;
         g.final_call = 0;
         if (!join()) return CTV_ECUDA;
-        fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
+        fgp_gap_list_kernel<<<gap_grid, GAP_NT, 0, s>>>(g);
         if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
         ++launches;
         if (!fork()) return CTV_ECUDA;
@@ -300,7 +346,7 @@ static ctv_status plan_enqueue(ctv_plan* P, cudaStream_t s, const cudaStream_t* 
   g.iter = K;
   g.final_call = 1;
   if (!join()) return CTV_ECUDA;
-  fgp_gap_list_kernel<<<P->n_gap, GAP_NT, 0, s>>>(g);
+  fgp_gap_list_kernel<<<gap_grid, GAP_NT, 0, s>>>(g);
   if (cudaGetLastError() != cudaSuccess) return CTV_ECUDA;
   ++launches;
   P->launches_per_execute = launches;

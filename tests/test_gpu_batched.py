@@ -89,6 +89,30 @@ def test_plan_gap_stopping_per_image():
         assert torch.equal(x1, im["x"])
 
 
+def test_plan_gap_runs_span_images():
+    # about 6000 gap tiles, more than the resident blocks of the gap / finalize
+    # launch, so each block evaluates a run of tiles that crosses image borders;
+    # per-image stopping, final statistics and x agree with one-image solves
+    shapes, lams, types, imgs = make_batch(48, 150, 260, seed=12)
+    ims = plan_images(imgs, lams, types)
+    plan = ctv.Plan(ims, 200, check_every=10, gap_tol=1e-4)
+    plan.execute()
+    st = plan.stats()
+    stopped = 0
+    for i, im in enumerate(ims):
+        tv = TV_NAMES[int(types[i])]
+        x1, s1 = ctv.denoise(im["b"], float(lams[i]), tv, 200, im["C"], 0.5, check_every=10, gap_tol=1e-4,
+                             config=plan.info()["config"], return_stats=True)
+        assert st[i]["iters"] == s1["iters"] and st[i]["stopped"] == s1["stopped"]
+        stopped += int(s1["stopped"])
+        assert torch.equal(x1, im["x"])
+        # FP64 sums of FP32 tile partials, added in another order
+        for key in ("primal", "dual"):
+            assert st[i][key] == pytest.approx(s1[key], rel=1e-12)
+        assert st[i]["gap"] == pytest.approx(s1["gap"], rel=1e-9, abs=1e-12 * abs(s1["primal"]))
+    assert 0 < stopped < len(ims)
+
+
 def test_plan_full_workload_sampled():
     # 512 images, sides log-uniform in [64, 1024], lambda ~ U[0.01, 0.1], mixed TV types, 100 iterations
     shapes, lams, types, imgs = make_batch(512, 64, 1024, seed=2021)
