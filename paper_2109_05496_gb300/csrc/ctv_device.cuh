@@ -334,8 +334,15 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
 
   const float lam = I.lam;
   const float c8 = lam > 0.f ? 1.f / (8.f * lam) : 0.f;
-  const bool has_right = lk < RW - 1 && (!EDGE || gk < I.n - 1);
+  const bool has_right = lk < RW - 1 && (!EDGE || (gk >= 0 && gk < I.n - 1));
   const bool strip_bottom_in = lj0 + PPT < RH;
+  // Pixels outside the image start at b = q = r = 0 and stay there when their
+  // forward differences are masked (rows j < 0 or j >= m - 1 have no d1,
+  // columns k < 0 or k >= n - 1 no d2) and P_C(0) = 0: then L^T r and hence x
+  // vanish there. That holds for no constraint, the amplitude bound and the
+  // support rectangle, so their edge path needs no per-pixel image test in
+  // the iterations; the general constraint (mask, box) keeps the tests.
+  constexpr bool TESTS = EDGE && CONS == CONS_GEN;
   for (int it = 0; it < nsteps; ++it) {
     // Rows whose values can still reach the interior after the remaining steps:
     // step it must produce q, r on rows [lo, RH - lo) and x on one more row.
@@ -351,7 +358,7 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
       const int gj = gj0 + s;
       if (SKIP_ROWS && (lj0 + s < lo || lj0 + s > hi)) continue;
       x[s] = z2;
-      if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
+      if (!TESTS || (colin && (unsigned)gj < (unsigned)I.m)) {
         float2 up;
         if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
         else up = wy > 0 ? P1B[(wy - 1) * RW + lk] : z2;
@@ -371,9 +378,9 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
     for (int s = 0; s < PPT; ++s) {
       const int gj = gj0 + s;
       if (SKIP_ROWS && (lj0 + s < lo || lj0 + s >= hi)) continue;
-      if (colin && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
+      if (!TESTS || (colin && (unsigned)gj < (unsigned)I.m)) {
         float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-        if (!EDGE || gj < I.m - 1) {
+        if (!EDGE || (gj >= 0 && gj < I.m - 1)) {
           float2 xd;
           if (s < PPT - 1) xd = x[s + 1];
           else xd = strip_bottom_in ? X[(lj0 + s + 1) * RW + lk] : x[s];
@@ -390,7 +397,8 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
         r[s] = f4(qn.x + bt * (qn.x - q[s].x), qn.y + bt * (qn.y - q[s].y),
                   qn.z + bt * (qn.z - q[s].z), qn.w + bt * (qn.w - q[s].w));
         q[s] = qn;
-        if (HIST && lk >= T && lk < RW - T && lj0 + s >= T && lj0 + s < RH - T)
+        if (HIST && lk >= T && lk < RW - T && lj0 + s >= T && lj0 + s < RH - T &&
+            (!EDGE || (colin && (unsigned)gj < (unsigned)I.m)))
           I.r_hist[it * I.hist_plane + (long long)gj * I.n + gk] = r[s];
       }
       P2[(lj0 + s) * RW + lk] = make_float2(r[s].z, r[s].w);
