@@ -29,8 +29,10 @@
 namespace ctv {
 
 // Grid front end of gap_tile: blockIdx.z is the image of an equally sized batch.
+// (six resident blocks per SM: 40 registers, no spills; the tile loop is
+// latency-bound, so more blocks in flight hide more of each tile's loads)
 template <int TV>
-__global__ void __launch_bounds__(GAP_NT) fgp_gap_kernel(GapParams p) {
+__global__ void __launch_bounds__(GAP_NT, 6) fgp_gap_kernel(GapParams p) {
   __shared__ float4 qs[GAP_RW * GAP_RH];
   __shared__ float2 xs[GAP_RW * GAP_RH];
   __shared__ double red[3 * (GAP_NT / 32)];

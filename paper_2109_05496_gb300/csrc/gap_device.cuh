@@ -39,12 +39,19 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
   const int tid = threadIdx.x;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float lam = g.lam;
+  // b of the thread's own pixels is loaded with q, so that a tile waits on one
+  // round of global loads; both later phases take it from registers
+  float2 bv[PPT];
 #pragma unroll
   for (int s = 0; s < PPT; ++s) {
     const int i = tid + s * NT;
     const int gj = gj0 + i / RW, gk = gk0 + i % RW;
     float4 v = z4;
-    if (g.q != nullptr && (unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) v = __ldg(g.q + (long long)gj * n + gk);
+    bv[s] = make_float2(0.f, 0.f);
+    if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
+      if (g.q != nullptr) v = __ldg(g.q + (long long)gj * n + gk);
+      bv[s] = __ldg(g.b + (long long)gj * g.ld + gk);
+    }
     qs[i] = v;
   }
   __syncthreads();
@@ -58,7 +65,7 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
       const float4 qc = qs[i];
       const float4 qu = lj > 0 ? qs[i - RW] : z4;
       const float4 ql = lk > 0 ? qs[i - 1] : z4;
-      const float2 bb = __ldg(g.b + (long long)gj * g.ld + gk);
+      const float2 bb = bv[s];
       xv = proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)),
                   gj, gk, g.C);
     }
@@ -75,7 +82,7 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
       const float4 qc = qs[i];
       const float4 qu = qs[i - RW];
       const float4 ql = qs[i - 1];
-      const float2 bb = __ldg(g.b + (long long)gj * g.ld + gk);
+      const float2 bb = bv[s];
       const float dlr = lam * (qc.x - qu.x + qc.z - ql.z);   // lam (L^T q)
       const float dli = lam * (qc.y - qu.y + qc.w - ql.w);
       const float wr = bb.x - dlr, wi = bb.y - dli;

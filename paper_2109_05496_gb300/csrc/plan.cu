@@ -116,7 +116,7 @@ __device__ __forceinline__ void list_gap_commit(const PlanImg* d, double (&acc)[
 // while the image stays the same and commits them - one block reduction and one
 // set of atomics - when the image changes or the run ends. A commit counts the
 // tiles it covers, so an image's reduction completes with its last tile.
-__global__ void __launch_bounds__(GAP_NT) fgp_gap_list_kernel(ListGapParams p) {
+__global__ void __launch_bounds__(GAP_NT, 4) fgp_gap_list_kernel(ListGapParams p) {
   __shared__ float4 qs[GAP_RW * GAP_RH];
   __shared__ float2 xs[GAP_RW * GAP_RH];
   __shared__ double red[3 * (GAP_NT / 32)];
