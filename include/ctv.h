@@ -251,9 +251,10 @@ void ctv_plan_destroy(ctv_plan* plan);
  * opts->alpha, opts->config (a configuration the recompute supports, else the
  * default); warm_start must be 0.
  * ctv_unrolled_forward writes x = x_K and keeps the state every ckpt_every
- * iterations in the workspace; ctv_unrolled_backward takes xbar = dL/dx and
+ * iterations in the workspace, together with every r_k of the last
+ * checkpoint segment; ctv_unrolled_backward takes xbar = dL/dx and
  * returns bbar = dL/db (complex64, same layout as b) and lambdabar = dL/dlambda
- * (DEVICE float per image), recomputing each checkpoint segment. The workspace
+ * (DEVICE float per image), recomputing each earlier checkpoint segment. The workspace
  * (ctv_unrolled_workspace_size bytes) must be the one the forward call used and
  * must not be touched in between.
  * -------------------------------------------------------------------------- */

@@ -915,6 +915,11 @@ int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const 
   nesterov_betas(K, &beta);
   PassParams p = base_pass(a, cons);
   const dim3 grid = pass_grid(cfg, m, n, batch);
+  const long long plane = (long long)(al((size_t)batch * m * n * sizeof(float4)) / sizeof(float4));
+  // The passes of the last checkpoint segment run as recompute passes and keep
+  // its r_k history (plane j holds r_{k0+2+j}, as the backward walk reads it),
+  // so the backward starts walking at once instead of recomputing that segment.
+  const int k0_last = ((K + c - 1) / c - 1) * c;
   int k = 1, out = 0;
   const float4* qin = nullptr;
   const float4* rin = nullptr;
@@ -934,7 +939,12 @@ int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const 
     p.r_in = rin;
     p.q_out = qo;
     p.r_out = ro;
-    if (launch_pass(tv_type, cfg, p, grid, s) != cudaSuccess) return CTV_ECUDA;
+    if (k > k0_last) {
+      if (launch_hist(tv_type, cfg, p, grid, L.hist + (long long)(k - k0_last - 1) * plane, plane, s) != cudaSuccess)
+        return CTV_ECUDA;
+    } else if (launch_pass(tv_type, cfg, p, grid, s) != cudaSuccess) {
+      return CTV_ECUDA;
+    }
     count_launch();
     qin = qo;
     rin = ro;
@@ -1012,14 +1022,15 @@ int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* la
   PassParams p = base_pass(a, cons);
   const dim3 grid = pass_grid(cfg, m, n, batch);
   const int nseg = (K + c - 1) / c;
-  // each segment: recompute it from its checkpoint (storing every r_k), then walk it back
+  // each segment: recompute it from its checkpoint (storing every r_k), then walk
+  // it back; the forward left the history of the last segment in place
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * c, k1 = std::min(k0 + c, K);
     // recompute iterations k0+1 .. k1-1, keeping r_{k0+2} .. r_{k1}
     const float4* qin = sg == 0 ? nullptr : L.ckq[(size_t)sg];
     const float4* rin = sg == 0 ? nullptr : L.ckr[(size_t)sg];
     bool first = sg == 0;
-    int kk = k0 + 1, out = 0;
+    int kk = sg == nseg - 1 ? k1 : k0 + 1, out = 0;
     while (kk <= k1 - 1) {
       const int steps = std::min(T, k1 - 1 - kk + 1);
       for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)kk + i] : 0.f;
