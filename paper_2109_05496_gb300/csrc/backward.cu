@@ -951,7 +951,7 @@ int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const 
     first = false;
     k = kend + 1;
   }
-  if (cudaMemsetAsync(L.st, 0, (size_t)batch * sizeof(DevStats), s) != cudaSuccess) return CTV_ECUDA;
+  // x_K = P_C(b - lam L^T q_K) (Eq. (18)); nobody reads objective terms here
   GapParams g;
   memset(&g, 0, sizeof(g));
   g.b = (const float2*)b;
@@ -968,10 +968,9 @@ int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const 
   g.lam_dev = lambdas;
   g.alpha = opts->alpha;
   g.C = cons;
-  g.st = L.st;
   g.iter = K;
   g.final_call = 1;
-  if (launch_gap(tv_type, g, batch, s) != cudaSuccess) return CTV_ECUDA;
+  if (launch_finalize(g, batch, s) != cudaSuccess) return CTV_ECUDA;
   count_launch();
   return CTV_OK;
 }

@@ -76,6 +76,8 @@ inline int cons_mode(const ConsDev& c) {
   return CONS_GEN;
 }
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s);
+// x = P_C(b - lam L^T q) only (no objective terms, no statistics record)
+cudaError_t launch_finalize(const GapParams& p, int batch, cudaStream_t s);
 // Grid of the fused pass for configuration cfg over an m x n image batch.
 dim3 pass_grid(int cfg, int m, int n, int batch);
 
