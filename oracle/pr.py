@@ -25,7 +25,7 @@ the previous q with t reset to 1.
 from __future__ import annotations
 
 import math
-from typing import Optional
+from typing import Callable, Optional
 
 import torch
 
@@ -77,23 +77,34 @@ def fidelity_grad(x: torch.Tensor, sqrt_y: torch.Tensor, H: torch.Tensor) -> tor
 
 def fista_pr(x0, sqrt_y, H, tau: float, gamma: float, outer: int, inner: int = 10,
              tv_type: str = "tv1_aniso", alpha: float = 0.5, C: Optional[Constraint] = None,
-             accelerate: bool = True, warm_start: bool = True, record_loss: bool = False):
+             accelerate: bool = True, warm_start: bool = True, record_loss: bool = False,
+             F: Optional[Callable] = None, grad_F: Optional[Callable] = None,
+             callback: Optional[Callable] = None):
     """Algorithm 1 (accelerate=True) or ISTA, Eq. (14) (accelerate=False).
 
+    F and grad_F default to the fidelity of Eq. (24) and its gradient, Eq. (27),
+    for (sqrt_y, H); a caller may pass another smooth fidelity (a complex image
+    in, a float or a complex image out) to run the same iteration on it.
+    callback(k, x_k), if given, sees every iterate (k = 1 .. outer).
     Returns (x_K, losses) where losses[k] = F(z_k) when record_loss is set."""
     x0 = torch.as_tensor(x0).to(CT)
-    sqrt_y = torch.as_tensor(sqrt_y).to(DT)
-    H = torch.as_tensor(H).to(CT)
+    if F is None or grad_F is None:
+        sqrt_y = torch.as_tensor(sqrt_y).to(DT)
+        H = torch.as_tensor(H).to(CT)
+    if F is None:
+        F = lambda x: fidelity(x, sqrt_y, H)           # noqa: E731
+    if grad_F is None:
+        grad_F = lambda x: fidelity_grad(x, sqrt_y, H)  # noqa: E731
     lam = tau * gamma
     z = x0.clone()
     x_prev = x0.clone()
     t = 1.0
     q = None
     losses = []
-    for _ in range(outer):
+    for k in range(1, outer + 1):
         if record_loss:
-            losses.append(fidelity(z, sqrt_y, H))
-        v = z - gamma * fidelity_grad(z, sqrt_y, H)
+            losses.append(F(z))
+        v = z - gamma * grad_F(z)
         res = fgp((v.real.clone(), v.imag.clone()), lam, inner, tv_type, alpha, C,
                   q0=q if warm_start else None)
         q = res.q
@@ -105,6 +116,8 @@ def fista_pr(x0, sqrt_y, H, tau: float, gamma: float, outer: int, inner: int = 1
         else:
             z = x
         x_prev = x
+        if callback is not None:
+            callback(k, x)
     return x_prev, losses
 
 

@@ -146,3 +146,80 @@ def test_line_search_reduces_to_fixed_step_and_backtracks():
     rhs = pr.fidelity(z, sqrt_y, H) + float((d.real * g.real + d.imag * g.imag).sum()) + \
         float((d.abs() ** 2).sum()) / (2 * gam[0])
     assert pr.fidelity(x1, sqrt_y, H) <= rhs
+
+
+def _ill_conditioned_quadratic(m, n, seed, spread):
+    """F(x) = 1/2 sum mu |x - c|^2 with mu spread log-uniformly over [spread, 1]:
+    convex, gradient Lipschitz constant L = 1, minimiser x* = c, F* = 0."""
+    g = torch.Generator().manual_seed(seed)
+    mu = torch.logspace(math.log10(spread), 0.0, m * n, dtype=DT).reshape(m, n)
+    mu = mu.flatten()[torch.randperm(m * n, generator=g)].reshape(m, n)
+    c = rand_c(m, n, seed + 1)
+
+    def F(x):
+        return 0.5 * float((mu * (x - c).abs() ** 2).sum())
+
+    def grad_F(x):
+        return mu * (x - c)
+
+    return F, grad_F, c
+
+
+def test_fista_momentum_beck_teboulle_rate():
+    # With tau = 0 and no constraint the prox of Algorithm 1 is the identity, so the
+    # iteration is accelerated gradient descent on F. Beck and Teboulle (2009),
+    # Theorem 4.4: with step gamma = 1/L, F(x_k) - F* <= 2 ||x_0 - x*||^2 / (gamma (k+1)^2)
+    # for every k >= 1. ISTA (Eq. (14)) only has an O(1/k) rate, and on this
+    # ill-conditioned F it leaves that bound, so an iteration that lost its momentum
+    # fails here. (A wrong extrapolation weight can still meet the bound; the
+    # estimate-sequence identity below is the pin for the weight itself.)
+    m = n = 16
+    F, grad_F, c = _ill_conditioned_quadratic(m, n, 21, 1e-4)
+    x0 = torch.zeros(m, n, dtype=CT)
+    R2 = float(((x0 - c).abs() ** 2).sum())
+    K, gamma = 300, 1.0
+
+    def run(accelerate):
+        vals = []
+        pr.fista_pr(x0, None, None, 0.0, gamma, K, 1, "tv1_aniso", 0.5, None, accelerate=accelerate,
+                    F=F, grad_F=grad_F, callback=lambda k, x: vals.append(F(x)))
+        return vals
+
+    fista, ista = run(True), run(False)
+    assert len(fista) == K
+    for k in range(1, K + 1):
+        assert fista[k - 1] <= 2.0 * R2 / (gamma * (k + 1) ** 2)
+    assert any(ista[k - 1] > 2.0 * R2 / (gamma * (k + 1) ** 2) for k in range(1, K + 1))
+    assert fista[199] < 0.1 * ista[199]
+
+
+def test_fista_momentum_estimate_sequence_identity():
+    # Nesterov's method in its two-sequence form (Tseng 2008; the u_k of Beck and
+    # Teboulle's proof of Theorem 4.4 is v_k - x*): with no prox to apply,
+    #     v_k = x_{k-1} + t_k (x_k - x_{k-1})   obeys   v_k = v_{k-1} - gamma t_k grad F(z_k),
+    # v_0 = x_0, where z_k is the point whose gradient step gave x_k and t_k is the
+    # positive root of t_k^2 - t_k = t_{k-1}^2 (t_1 = 1). It holds only for the
+    # extrapolation weight (t_k - 1)/t_{k+1} of Algorithm 1, step 5.
+    m, n = 12, 10
+    F, grad_F, c = _ill_conditioned_quadratic(m, n, 31, 1e-3)
+    x0 = rand_c(m, n, 33)
+    gamma, K = 0.8, 60
+    zs, xs = [], [x0]
+
+    def grad_rec(z):
+        zs.append(z.clone())
+        return grad_F(z)
+
+    pr.fista_pr(x0, None, None, 0.0, gamma, K, 1, "tv1_aniso", 0.5, None, F=F, grad_F=grad_rec,
+                callback=lambda k, x: xs.append(x.clone()))
+    assert len(zs) == K and len(xs) == K + 1
+    t = [None, 1.0]
+    for _ in range(K):
+        tp = t[-1]
+        t.append(0.5 + math.sqrt(0.25 + tp * tp))   # root of s^2 - s - tp^2 = 0
+    v_prev = x0
+    for k in range(1, K + 1):
+        v = xs[k - 1] + t[k] * (xs[k] - xs[k - 1])
+        want = v_prev - gamma * t[k] * grad_F(zs[k - 1])
+        assert float((v - want).abs().max()) <= 1e-10 * max(1.0, float(want.abs().max()))
+        v_prev = v
