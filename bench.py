@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the short runs of the other workloads after the headline")
     ap.add_argument("--workload", default="denoise2048",
                     choices=("denoise2048", "denoise2048_stop", "denoise256", "batched", "pr", "backward",
                              "pr_paper"),
@@ -252,9 +254,10 @@ def main():
     ms = e0.elapsed_time(e1)
     pass_ms, pass_n, units, all_n = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
     lib.ctv_profile_read(ctypes.byref(pass_ms), ctypes.byref(pass_n), ctypes.byref(units), ctypes.byref(all_n))
-    # the same steps again with every fused-pass launch bracketed by CUDA events on its stream,
-    # for the roofline's per-launch kernel time (kept out of the timed steps above)
-    lib.ctv_profile_enable(1)
+    # the same steps again with each solve's run of fused-pass launches bracketed by two CUDA
+    # events on its stream (the passes inside a run keep their back-to-back overlap), for the
+    # roofline's kernel time per launch (kept out of the timed steps above)
+    lib.ctv_profile_enable(2)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     for i in range(args.steps):
@@ -331,7 +334,26 @@ def main():
             "algorithmic_bytes_per_pixel_iter": ALGO_BYTES_PER_PX_IT,
             "pixel_iters_per_launch": per_launch_units,
             "avg_launch_us": pass_ms.value * 1e3 / max(pass_n.value, 1),
-            "kernel_share_of_step": pass_ms.value / ms_profiled if ms_profiled > 0 else None}
+            "timing": "CUDA events around each solve's run of back-to-back pass launches (one run of "
+                      "%d launches per solve), in a second pass over the timed steps" %
+                      (pass_n.value // max(args.steps * len(TVS), 1)),
+            "kernel_ms_per_step": pass_ms.value / args.steps,
+            "kernel_share_of_step": pass_ms.value / ms_profiled if ms_profiled > 0 else None,
+            "traffic_note": "ncu DRAM bytes per launch averaged over consecutive launches with "
+                            "--cache-control none (a launch's dirty L2 lines are written back during the "
+                            "next one)"}
+
+    # the other workloads of the metric (batched vs looped; 256^2 latency; gap stopping;
+    # phase retrieval; backward), each briefly, on rank 0 of a single-GPU run
+    workloads = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        workloads = {}
+        wl_steps = 5
+        workloads["batched"] = measure_batched(ctv, dev, wl_steps, 3)
+        workloads["denoise256"] = measure_denoise256(ctv, dev, 50, 3, [default_config_small(lib)])
+        workloads["denoise2048_stop"] = measure_stop(ctv, dev, 2)
+        workloads["pr"] = measure_pr(ctv, dev, 1)
+        workloads["backward"] = measure_backward(ctv, dev, wl_steps, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -363,6 +385,16 @@ def main():
                           "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single"},
                "e2e": e2e, "gpu_launches": int(all_n.value), "roofline": roof, "cpu_baseline": cpu,
                "clocks": clocks}
+        if workloads is not None:
+            bt = workloads["batched"]
+            out["batched"] = {"value": bt["value"], "looped_value": bt["looped_value"],
+                              "speedup_vs_loop": bt["speedup_vs_loop"],
+                              "speedup_vs_loop_same_config": bt["speedup_vs_loop_same_config"],
+                              "unit": UNIT, "accuracy": bt["accuracy"],
+                              "workload": "512 complex64 images, sides log-uniform in [64, 1024], lambda ~ "
+                                          "U[0.01, 0.1], mixed TV types, 100 iterations: one plan graph replay "
+                                          "vs a per-image loop of ctv_denoise"}
+            out["workloads"] = workloads
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -372,288 +404,341 @@ def default_config_id(lib) -> int:
     return int(lib.ctv_default_config(M, N, ITERS, 0))
 
 
+def default_config_small(lib) -> int:
+    return int(lib.ctv_default_config(256, 256, 100, 0))
+
+
 # ----------------------------------------------------------------------------- other workloads
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def measure_denoise256(ctv, dev, steps, warmup, configs):
+    """C1: 256^2 phantom, sigma 0.1, lambda 0.05, |x| <= 1, TV1 iso, 100 iterations;
+    plain calls and a CUDA graph, per configuration."""
+    import torch
+    from phantoms import noisy_phantom, to_c64
+    _, noisy = noisy_phantom(256, 256, 0.1, seed=1)
+    b = torch.from_numpy(to_c64(noisy)).to(dev)
+    x = torch.empty_like(b)
+    ws = ctv.workspace(1, 256, 256, dev)
+    C = ctv.Constraint(amp_max=1.0)
+    res = {}
+    for cfg in configs:
+        opts = ctv.make_opts(100, config=cfg)
+        for _ in range(warmup):
+            ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(steps):
+            ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_us = e0.elapsed_time(e1) * 1e3 / steps
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = e0.elapsed_time(e1) * 1e3 / steps
+        res[cfg] = {"us_per_solve": plain_us, "us_per_solve_graph": graph_us,
+                    "gpx_it_s_graph": 256 * 256 * 100 / (graph_us * 1e-6) / 1e9}
+    best = min(res, key=lambda c: res[c]["us_per_solve_graph"])
+    return {"metric": "FGP 256x256 solve time (100 iterations)", "value": res[best]["us_per_solve_graph"],
+            "unit": "us/solve", "higher_is_better": False, "configs": res, "best_config": best}
+
+
+def measure_batched(ctv, dev, steps, warmup, config=-1):
+    """C4: 512 images, sides log-uniform in [64, 1024], lambda ~ U[0.01, 0.1], mixed TV
+    types, 100 iterations: one graph replay of a plan against a per-image loop of
+    ctv_denoise. Equal accuracy: the same 100 iterations on every image; the loop
+    with the plan's configuration reproduces the plan's x bit for bit, and the
+    loop with each image's default configuration agrees with it within 1e-4 ||b||_inf."""
+    import torch
+    from phantoms import batch_params, batch_shapes, noisy_phantom, to_c64
+    shapes = batch_shapes(512, 64, 1024, seed=2021)
+    lams, types = batch_params(512, seed=2022)
+    ims = []
+    for i, (m, n) in enumerate(shapes):
+        _, noisy = noisy_phantom(m, n, 0.1, seed=2021000 + i)
+        bb = torch.from_numpy(to_c64(noisy)).to(dev)
+        ims.append({"b": bb, "x": torch.empty_like(bb), "lam": float(lams[i]), "tv": TVS[int(types[i])],
+                    "alpha": 0.5, "C": ctv.Constraint(amp_max=1.0)})
+    plan = ctv.Plan(ims, 100, config=config)
+    info = plan.info()
+    for _ in range(warmup):
+        plan.execute()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(steps):
+        plan.execute()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plan = e0.elapsed_time(e1) / steps
+    x_plan = [im["x"].clone() for im in ims]
+    wss = {}
+    for im in ims:
+        key = tuple(im["b"].shape)
+        if key not in wss:
+            wss[key] = ctv.workspace(1, key[0], key[1], dev)
+
+    def loop(opts):
+        for im in ims:
+            ctv.ctv_denoise(im["b"], im["x"], im["lam"], im["C"], im["tv"], opts, ws=wss[tuple(im["b"].shape)])
+
+    def time_loop(opts, reps):
+        loop(opts)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            loop(opts)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, steps // 3)
+    # the loop a user writes: every image with the library's default configuration for its size
+    ms_loop = time_loop(ctv.make_opts(100), reps)
+    worst = 0.0
+    for im, xp in zip(ims, x_plan):
+        worst = max(worst, float((im["x"] - xp).abs().max()) / max(float(im["b"].abs().max()), 1e-30))
+    # and the loop with the plan's own configuration
+    ms_loop_same = time_loop(ctv.make_opts(100, config=info["config"]), reps)
+    same_bits = all(torch.equal(im["x"], xp) for im, xp in zip(ims, x_plan))
+    pxit = info["pixel_iters"]
+    return {"metric": "batched FGP Gpixel-iter/s (512 uneven images, one graph replay) vs per-image loop",
+            "value": pxit / (ms_plan * 1e-3) / 1e9, "unit": "Gpixel-iter/s", "higher_is_better": True,
+            "ms_per_batch": ms_plan, "looped_ms_per_batch": ms_loop,
+            "looped_value": pxit / (ms_loop * 1e-3) / 1e9, "speedup_vs_loop": ms_loop / ms_plan,
+            "looped_same_config_ms_per_batch": ms_loop_same,
+            "speedup_vs_loop_same_config": ms_loop_same / ms_plan,
+            "accuracy": {"iterations": 100, "loop_same_config_bit_identical": same_bits,
+                         "loop_default_config_max_dx_over_binf": worst, "tol": 1e-4},
+            "plan": info, "images": 512, "megapixels": pxit / 100 / 1e6}
+
+
+def measure_pr(ctv, dev, warmup):
+    """C3: 1024^2 object, Fresnel TF (532 nm, 2 um, 5 mm), 2x padding, Poisson 1e4 photons,
+    300 outer x 10 inner iterations, tau 0.01."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_2109_05496_gb300 import _lib
+    from phantoms import fresnel_tf, pr_object, simulate_intensity
+    m = n = 1024
+    Mp = Np = 2048
+    H = fresnel_tf(Mp, Np, 532e-9, 2e-6, 5e-3).astype(np.complex64)
+    x_gt = pr_object(m, n, seed=11)
+    y = simulate_intensity(x_gt, H.astype(np.complex128), seed=12, photons=1e4)
+    sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
+    Hg = torch.from_numpy(H).to(dev)
+    plan = ctv.PRPlan(m, n, Mp, Np)
+    x0 = torch.empty(m, n, dtype=torch.complex64, device=dev)
+    g, _ = plan.gradient(torch.zeros_like(x0), sqrt_y, Hg)
+    x0.copy_(-g)                    # A^* sqrt(y): the gradient at 0 is -A^*(sqrt(y))
+    outer = 300
+    C = ctv.Constraint(amp_max=1.0)
+    # warm-up: full solves, long enough for the clocks to settle
+    for _ in range(warmup):
+        plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    xk, hist = plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer, return_loss=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    xg = xk.cpu().numpy()
+    ph = np.angle(xg * np.conj(x_gt))
+    ph = np.angle(np.exp(1j * (ph - np.angle(np.exp(1j * ph).mean()))))
+    ph0 = np.angle(x0.cpu().numpy() * np.conj(x_gt))
+    ph0 = np.angle(np.exp(1j * (ph0 - np.angle(np.exp(1j * ph0).mean()))))
+    h = hist.cpu().numpy()
+    # where the time goes: the fused FGP pass runs (timed per run of passes in a second solve)
+    # and one gradient evaluation (two 2048^2 FFT pairs, the fused residual and the adjoint crop)
+    lib = _lib.load()
+    lib.ctv_profile_enable(2)
+    plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
+    pass_ms, pass_n, units, all_n = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
+    lib.ctv_profile_read(ctypes.byref(pass_ms), ctypes.byref(pass_n), ctypes.byref(units), ctypes.byref(all_n))
+    lib.ctv_profile_enable(0)
+    reps = 50
+    g0, g1 = _events()
+    g0.record()
+    for _ in range(reps):
+        plan.gradient(x0, sqrt_y, Hg)
+    g1.record()
+    torch.cuda.synchronize()
+    grad_ms = g0.elapsed_time(g1) / reps
+    return {"metric": "phase retrieval outer iterations/s (1024^2 object, 2048^2 FFTs, 10 FGP iterations each)",
+            "value": outer / (ms * 1e-3), "unit": "outer-iter/s", "higher_is_better": True,
+            "ms_total": ms, "fgp_pixel_iters": outer * 10 * m * n,
+            "fgp_pass_ms_total": pass_ms.value,
+            "fgp_pass_gpx_it_s": units.value / (pass_ms.value * 1e-3) / 1e9 if pass_ms.value > 0 else None,
+            "gradient_ms_per_outer": grad_ms, "gradient_share": grad_ms * outer / ms,
+            "fgp_pass_share": pass_ms.value / ms,
+            "loss_first": float(h[0]), "loss_last": float(h[-1]),
+            "phase_rmse_initial": float(np.sqrt((ph0 ** 2).mean())),
+            "phase_rmse_final": float(np.sqrt((ph ** 2).mean()))}
+
+
+def measure_stop(ctv, dev, steps, config=-1):
+    """C2 with stopping: the 36 solves of the headline workload with the duality-gap
+    test on (checked every 10 iterations, stop at gap <= 1e-6 P, at most 200
+    iterations): iterations to stop and time per solve."""
+    import numpy as np
+    import torch
+    imgs_np, rect = make_inputs(0)
+    hm, hn = imgs_np[0].shape
+    C = ctv.Constraint(amp_max=1.0, rect=rect)
+    ws = ctv.workspace(1, hm, hn, dev)
+    x = torch.empty(hm, hn, dtype=torch.complex64, device=dev)
+    solves, tot_ms, tot_pxit = [], 0.0, 0.0
+    for ci, (sigma, lam) in enumerate(combos()):
+        b = torch.from_numpy(imgs_np[ci]).to(dev)
+        for tv in TVS:
+            opts = ctv.make_opts(ITERS, 10, 1e-6, 0.5, False, config)
+            st = ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws, want_stats=True)
+            ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws)   # the library builds its stop graph here
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record()
+            for _ in range(steps):
+                ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / steps
+            solves.append({"sigma": sigma, "lambda": lam, "tv": tv, "k_stop": st["iters"],
+                           "stopped": st["stopped"], "gap_rel": st["gap"] / max(st["primal"], 1e-30),
+                           "ms": t})
+            tot_ms += t
+            tot_pxit += st["iters"] * hm * hn
+    ks = [r["k_stop"] for r in solves]
+    return {"metric": "2048^2 solves with duality-gap stopping (gap <= 1e-6 P, checked every 10)",
+            "value": tot_ms / len(solves), "unit": "ms/solve", "higher_is_better": False,
+            "k_stop_mean": float(np.mean(ks)), "k_stop_min": int(min(ks)), "k_stop_max": int(max(ks)),
+            "stopped_before_200": int(sum(1 for r in solves if r["stopped"])),
+            "gpx_it_s_effective": tot_pxit / (tot_ms * 1e-3) / 1e9, "solves": solves}
+
+
+def measure_backward(ctv, dev, steps, warmup, config=-1):
+    """C5: 8 x 1024^2, 50 unrolled iterations, checkpoints every 10, loss ||x - x_gt||^2:
+    backward / forward time."""
+    import numpy as np
+    import torch
+    from phantoms import noisy_phantom, to_c64
+    Bn, m, n, K = 8, 1024, 1024, 50
+    cl, nz = [], []
+    for i in range(Bn):
+        c_, z_ = noisy_phantom(m, n, 0.1, seed=700 + i)
+        cl.append(to_c64(c_))
+        nz.append(to_c64(z_))
+    b = torch.from_numpy(np.stack(nz)).to(dev).requires_grad_(True)
+    gt = torch.from_numpy(np.stack(cl)).to(dev)
+    lam = torch.linspace(0.02, 0.09, Bn, device=dev).requires_grad_(True)
+    C = ctv.Constraint(amp_max=1.0)
+
+    def fwd():
+        return ctv.denoise_unrolled(b, lam, "tv1_iso", K, C, 0.5, 10, config)
+
+    for _ in range(warmup):
+        loss = ((fwd() - gt).abs() ** 2).sum()
+        loss.backward()
+    torch.cuda.synchronize()
+    tf = tb = 0.0
+    for _ in range(steps):
+        e0, e1 = _events()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x = fwd()
+        e1.record()
+        loss = ((x - gt).abs() ** 2).sum()
+        e3 = torch.cuda.Event(enable_timing=True)
+        e3.record()
+        loss.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        tf += e0.elapsed_time(e1)
+        tb += e3.elapsed_time(e2)
+    tf /= steps
+    tb /= steps
+    return {"metric": "unrolled FGP backward/forward time ratio (8 x 1024^2, 50 iterations, ckpt 10)",
+            "value": tb / tf, "unit": "ratio", "higher_is_better": False, "forward_ms": tf,
+            "backward_ms": tb, "forward_gpx_it_s": Bn * m * n * K / (tf * 1e-3) / 1e9}
+
+
+def measure_pr_paper(ctv, dev):
+    """The paper's simulated setting (Sec. VI-A): 256^2 pure phase object (phase in [0, pi]),
+    angular spectrum at 500 nm, 5 um pixels, 5 mm, 10% Gaussian intensity noise,
+    back-propagated start, type-I anisotropic TV, 10 FGP iterations per outer
+    iteration; IP vs TV (C = C^n) vs CTV."""
+    import numpy as np
+    import torch
+    from phantoms import angular_spectrum_tf, intensity_with_gaussian_noise, phase_object, phase_rmse
+    m = n = 256
+    H = angular_spectrum_tf(m, n, 500e-9, 5e-6, 5e-3).astype(np.complex64)
+    x_gt = phase_object(m, n, seed=31)
+    y = intensity_with_gaussian_noise(x_gt, H.astype(np.complex128), 0.1, seed=32)
+    sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
+    Hg = torch.from_numpy(H).to(dev)
+    plan = ctv.PRPlan(m, n, m, n)
+    g0, _ = plan.gradient(torch.zeros(m, n, dtype=torch.complex64, device=dev), sqrt_y, Hg)
+    x0 = (-g0).contiguous()
+    tau = 0.005
+    curves = {}
+    t0 = time.perf_counter()
+    for name in ("IP", "TV", "CTV"):
+        rm = []
+        for K in range(10, 151, 10):      # the state after K outer iterations, from x_0 each time
+            if name == "IP":
+                x = ctv.api.ip_solve(plan, x0, sqrt_y, Hg, K, ctv.Constraint(amp_max=1.0))
+            else:
+                C = ctv.Constraint(amp_max=1.0) if name == "CTV" else ctv.NO_CONSTRAINT
+                x = plan.solve(x0, sqrt_y, Hg, tau, 1.0, C, "tv1_aniso", 10, K)
+            rm.append(phase_rmse(x.cpu().numpy(), x_gt))
+        curves[name] = rm
+    dt = time.perf_counter() - t0
+    return {"metric": "phase RMSE (rad) after 50/100/150 outer iterations, paper's simulated setting",
+            "value": curves["CTV"][-1], "unit": "rad", "higher_is_better": False,
+            "rmse_initial": phase_rmse(x0.cpu().numpy(), x_gt),
+            "rmse_at_50_100_150": {k: [v[4], v[9], v[14]] for k, v in curves.items()},
+            "curves_every_10": curves, "tau": tau, "wall_s": dt}
+
+
 def run_other_workload(args, world, rank, local):
     """Secondary measurements, one JSON line each (single GPU)."""
-    import numpy as np
     import torch
     torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
     import paper_2109_05496_gb300 as ctv
-    from phantoms import (batch_params, batch_shapes, fresnel_tf, noisy_phantom, pr_object, simulate_intensity,
-                          to_c64)
     dev = torch.device("cuda", local)
     out = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
            "workload": args.workload}
     if args.workload == "denoise256":
-        # 256^2 phantom, sigma 0.1, lambda 0.05, |x| <= 1, TV1 iso, 100 iterations; plain calls and a CUDA graph
-        _, noisy = noisy_phantom(256, 256, 0.1, seed=1)
-        b = torch.from_numpy(to_c64(noisy)).to(dev)
-        x = torch.empty_like(b)
-        ws = ctv.workspace(1, 256, 256, dev)
-        C = ctv.Constraint(amp_max=1.0)
-        res = {}
-        for cfg in ([args.config] if args.config >= 0 else list(range(ctv._lib.load().ctv_num_configs()))):
-            opts = ctv.make_opts(100, config=cfg)
-            for _ in range(args.warmup):
-                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
-            torch.cuda.synchronize()
-            e0, e1 = _events()
-            e0.record()
-            for _ in range(args.steps):
-                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
-            e1.record()
-            torch.cuda.synchronize()
-            plain_us = e0.elapsed_time(e1) * 1e3 / args.steps
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=s):
-                ctv.ctv_denoise(b, x, 0.05, C, "tv1_iso", opts, ws=ws)
-            for _ in range(args.warmup):
-                g.replay()
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(args.steps):
-                g.replay()
-            e1.record()
-            torch.cuda.synchronize()
-            graph_us = e0.elapsed_time(e1) * 1e3 / args.steps
-            res[cfg] = {"us_per_solve": plain_us, "us_per_solve_graph": graph_us,
-                        "gpx_it_s_graph": 256 * 256 * 100 / (graph_us * 1e-6) / 1e9}
-        best = min(res, key=lambda c: res[c]["us_per_solve_graph"])
-        out.update({"metric": "FGP 256x256 solve time (100 iterations)", "value": res[best]["us_per_solve_graph"],
-                    "unit": "us/solve", "higher_is_better": False, "configs": res, "best_config": best})
+        cfgs = [args.config] if args.config >= 0 else list(range(ctv._lib.load().ctv_num_configs()))
+        out.update(measure_denoise256(ctv, dev, args.steps, args.warmup, cfgs))
     elif args.workload == "batched":
-        # 512 images, sides log-uniform in [64, 1024], lambda ~ U[0.01, 0.1], mixed TV, 100 iterations
-        shapes = batch_shapes(512, 64, 1024, seed=2021)
-        lams, types = batch_params(512, seed=2022)
-        tvs = ["tv1_iso", "tv1_aniso", "tv2_iso", "tv2_aniso"]
-        ims = []
-        for i, (m, n) in enumerate(shapes):
-            _, noisy = noisy_phantom(m, n, 0.1, seed=2021000 + i)
-            bb = torch.from_numpy(to_c64(noisy)).to(dev)
-            ims.append({"b": bb, "x": torch.empty_like(bb), "lam": float(lams[i]), "tv": tvs[int(types[i])],
-                        "alpha": 0.5, "C": ctv.Constraint(amp_max=1.0)})
-        cfg = args.config if args.config >= 0 else -1
-        plan = ctv.Plan(ims, 100, config=cfg)
-        info = plan.info()
-        for _ in range(args.warmup):
-            plan.execute()
-        torch.cuda.synchronize()
-        e0, e1 = _events()
-        e0.record()
-        for _ in range(args.steps):
-            plan.execute()
-        e1.record()
-        torch.cuda.synchronize()
-        ms_plan = e0.elapsed_time(e1) / args.steps
-        wss = {}
-        for im in ims:
-            key = tuple(im["b"].shape)
-            if key not in wss:
-                wss[key] = ctv.workspace(1, key[0], key[1], dev)
-
-        def loop(opts):
-            for im in ims:
-                ctv.ctv_denoise(im["b"], im["x"], im["lam"], im["C"], im["tv"], opts, ws=wss[tuple(im["b"].shape)])
-
-        def time_loop(opts):
-            loop(opts)
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(max(1, args.steps // 3)):
-                loop(opts)
-            e1.record()
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / max(1, args.steps // 3)
-
-        # the loop a user writes: every image with the library's default configuration for its size
-        ms_loop = time_loop(ctv.make_opts(100))
-        # and the loop with the plan's own configuration
-        ms_loop_same = time_loop(ctv.make_opts(100, config=info["config"]))
-        pxit = info["pixel_iters"]
-        out.update({"metric": "batched FGP Gpixel-iter/s (512 uneven images, one graph replay) vs per-image loop",
-                    "value": pxit / (ms_plan * 1e-3) / 1e9, "unit": "Gpixel-iter/s", "higher_is_better": True,
-                    "ms_per_batch": ms_plan, "looped_ms_per_batch": ms_loop,
-                    "looped_value": pxit / (ms_loop * 1e-3) / 1e9, "speedup_vs_loop": ms_loop / ms_plan,
-                    "looped_same_config_ms_per_batch": ms_loop_same,
-                    "speedup_vs_loop_same_config": ms_loop_same / ms_plan,
-                    "plan": info, "images": 512, "megapixels": pxit / 100 / 1e6})
+        out.update(measure_batched(ctv, dev, args.steps, args.warmup, args.config if args.config >= 0 else -1))
     elif args.workload == "pr":
-        # 1024^2 object, Fresnel TF (532 nm, 2 um, 5 mm), 2x padding, Poisson 1e4 photons, 300 x 10, tau 0.01
-        m = n = 1024
-        M = N = 2048
-        H = fresnel_tf(M, N, 532e-9, 2e-6, 5e-3).astype(np.complex64)
-        x_gt = pr_object(m, n, seed=11)
-        y = simulate_intensity(x_gt, H.astype(np.complex128), seed=12, photons=1e4)
-        sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
-        Hg = torch.from_numpy(H).to(dev)
-        plan = ctv.PRPlan(m, n, M, N)
-        x0 = torch.empty(m, n, dtype=torch.complex64, device=dev)
-        g, _ = plan.gradient(torch.zeros_like(x0), sqrt_y, Hg)
-        x0.copy_(-g)                    # A^* sqrt(y): the gradient at 0 is -A^*(sqrt(y))
-        outer = 300
-        C = ctv.Constraint(amp_max=1.0)
-        # warm-up: full solves, long enough for the clocks to settle (a few ms of work left the
-        # timed solve at a fraction of the steady rate)
-        for _ in range(args.warmup):
-            plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
-        torch.cuda.synchronize()
-        e0, e1 = _events()
-        e0.record()
-        xk, hist = plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer, return_loss=True)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        xg = xk.cpu().numpy()
-        ph = np.angle(xg * np.conj(x_gt))
-        ph = np.angle(np.exp(1j * (ph - np.angle(np.exp(1j * ph).mean()))))
-        ph0 = np.angle(x0.cpu().numpy() * np.conj(x_gt))
-        ph0 = np.angle(np.exp(1j * (ph0 - np.angle(np.exp(1j * ph0).mean()))))
-        h = hist.cpu().numpy()
-        # where the time goes: the fused FGP passes (timed per launch in a second, profiled run) and one
-        # gradient evaluation (two 2048^2 FFT pairs, the fused residual and the adjoint crop) per outer iteration
-        import ctypes
-        from paper_2109_05496_gb300 import _lib
-        lib = _lib.load()
-        lib.ctv_profile_enable(1)
-        plan.solve(x0, sqrt_y, Hg, 0.01, 1.0, C, "tv1_aniso", 10, outer)
-        pass_ms, pass_n, units, all_n = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
-        lib.ctv_profile_read(ctypes.byref(pass_ms), ctypes.byref(pass_n), ctypes.byref(units), ctypes.byref(all_n))
-        lib.ctv_profile_enable(0)
-        reps = 50
-        g0, g1 = _events()
-        g0.record()
-        for _ in range(reps):
-            plan.gradient(x0, sqrt_y, Hg)
-        g1.record()
-        torch.cuda.synchronize()
-        grad_ms = g0.elapsed_time(g1) / reps
-        out.update({"metric": "phase retrieval outer iterations/s (1024^2 object, 2048^2 FFTs, 10 FGP iterations each)",
-                    "value": outer / (ms * 1e-3), "unit": "outer-iter/s", "higher_is_better": True,
-                    "ms_total": ms, "fgp_pixel_iters": outer * 10 * m * n,
-                    "fgp_pass_ms_total": pass_ms.value, "fgp_pass_gpx_it_s": units.value / (pass_ms.value * 1e-3) / 1e9
-                    if pass_ms.value > 0 else None,
-                    "gradient_ms_per_outer": grad_ms, "gradient_share": grad_ms * outer / ms,
-                    "fgp_pass_share": pass_ms.value / ms,
-                    "loss_first": float(h[0]), "loss_last": float(h[-1]),
-                    "phase_rmse_initial": float(np.sqrt((ph0 ** 2).mean())),
-                    "phase_rmse_final": float(np.sqrt((ph ** 2).mean()))})
+        out.update(measure_pr(ctv, dev, args.warmup))
     elif args.workload == "denoise2048_stop":
-        # the 36 solves of the headline workload with the duality-gap test on (checked every 10 iterations,
-        # stop at gap <= 1e-6 P, at most 200 iterations): iterations to stop and time per solve
-        imgs_np, rect = make_inputs(0)
-        hm, hn = imgs_np[0].shape
-        C = ctv.Constraint(amp_max=1.0, rect=rect)
-        ws = ctv.workspace(1, hm, hn, dev)
-        x = torch.empty(hm, hn, dtype=torch.complex64, device=dev)
-        solves, tot_ms, tot_pxit = [], 0.0, 0.0
-        for ci, (sigma, lam) in enumerate(combos()):
-            b = torch.from_numpy(imgs_np[ci]).to(dev)
-            for tv in TVS:
-                opts = ctv.make_opts(ITERS, 10, 1e-6, 0.5, False, args.config)
-                st = ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws, want_stats=True)
-                ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws)   # the library builds its stop graph here
-                torch.cuda.synchronize()
-                e0, e1 = _events()
-                e0.record()
-                for _ in range(args.steps):
-                    ctv.ctv_denoise(b, x, lam, C, tv, opts, ws=ws)
-                e1.record()
-                torch.cuda.synchronize()
-                t = e0.elapsed_time(e1) / args.steps
-                solves.append({"sigma": sigma, "lambda": lam, "tv": tv, "k_stop": st["iters"],
-                               "stopped": st["stopped"], "gap_rel": st["gap"] / max(st["primal"], 1e-30),
-                               "ms": t})
-                tot_ms += t
-                tot_pxit += st["iters"] * hm * hn
-        ks = [r["k_stop"] for r in solves]
-        out.update({"metric": "2048^2 solves with duality-gap stopping (gap <= 1e-6 P, checked every 10)",
-                    "value": tot_ms / len(solves), "unit": "ms/solve", "higher_is_better": False,
-                    "k_stop_mean": float(np.mean(ks)), "k_stop_min": int(min(ks)), "k_stop_max": int(max(ks)),
-                    "stopped_before_200": int(sum(1 for r in solves if r["stopped"])),
-                    "gpx_it_s_effective": tot_pxit / (tot_ms * 1e-3) / 1e9, "solves": solves})
+        out.update(measure_stop(ctv, dev, args.steps, args.config))
     elif args.workload == "pr_paper":
-        # the paper's simulated setting (Sec. VI-A): 256^2 pure phase object (phase in [0, pi]),
-        # angular spectrum at 500 nm, 5 um pixels, 5 mm, 10% Gaussian intensity noise, back-propagated
-        # start, type-I anisotropic TV, 10 FGP iterations per outer iteration; IP vs TV (C = C^n) vs CTV
-        from phantoms import angular_spectrum_tf, intensity_with_gaussian_noise, phase_object, phase_rmse
-        m = n = 256
-        H = angular_spectrum_tf(m, n, 500e-9, 5e-6, 5e-3).astype(np.complex64)
-        x_gt = phase_object(m, n, seed=31)
-        y = intensity_with_gaussian_noise(x_gt, H.astype(np.complex128), 0.1, seed=32)
-        sqrt_y = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
-        Hg = torch.from_numpy(H).to(dev)
-        plan = ctv.PRPlan(m, n, m, n)
-        g0, _ = plan.gradient(torch.zeros(m, n, dtype=torch.complex64, device=dev), sqrt_y, Hg)
-        x0 = (-g0).contiguous()
-        tau = 0.005
-        curves = {}
-        t0 = time.perf_counter()
-        for name in ("IP", "TV", "CTV"):
-            rm = []
-            for K in range(10, 151, 10):      # the state after K outer iterations, from x_0 each time
-                if name == "IP":
-                    x = ctv.api.ip_solve(plan, x0, sqrt_y, Hg, K, ctv.Constraint(amp_max=1.0))
-                else:
-                    C = ctv.Constraint(amp_max=1.0) if name == "CTV" else ctv.NO_CONSTRAINT
-                    x = plan.solve(x0, sqrt_y, Hg, tau, 1.0, C, "tv1_aniso", 10, K)
-                rm.append(phase_rmse(x.cpu().numpy(), x_gt))
-            curves[name] = rm
-        dt = time.perf_counter() - t0
-        out.update({"metric": "phase RMSE (rad) after 50/100/150 outer iterations, paper's simulated setting",
-                    "value": curves["CTV"][-1], "unit": "rad", "higher_is_better": False,
-                    "rmse_initial": phase_rmse(x0.cpu().numpy(), x_gt),
-                    "rmse_at_50_100_150": {k: [v[4], v[9], v[14]] for k, v in curves.items()},
-                    "curves_every_10": curves, "tau": tau, "wall_s": dt})
+        out.update(measure_pr_paper(ctv, dev))
     elif args.workload == "backward":
-        # 8 x 1024^2, 50 unrolled iterations, checkpoints every 10, loss ||x - x_gt||^2
-        Bn, m, n, K = 8, 1024, 1024, 50
-        cl, nz = [], []
-        for i in range(Bn):
-            c_, z_ = noisy_phantom(m, n, 0.1, seed=700 + i)
-            cl.append(to_c64(c_))
-            nz.append(to_c64(z_))
-        b = torch.from_numpy(np.stack(nz)).to(dev).requires_grad_(True)
-        gt = torch.from_numpy(np.stack(cl)).to(dev)
-        lam = torch.linspace(0.02, 0.09, Bn, device=dev).requires_grad_(True)
-        C = ctv.Constraint(amp_max=1.0)
-        cfg = args.config if args.config >= 0 else -1
-
-        def fwd():
-            return ctv.denoise_unrolled(b, lam, "tv1_iso", K, C, 0.5, 10, cfg)
-
-        for _ in range(args.warmup):
-            loss = ((fwd() - gt).abs() ** 2).sum()
-            loss.backward()
-        torch.cuda.synchronize()
-        tf = tb = 0.0
-        for _ in range(args.steps):
-            e0, e1 = _events()
-            e2 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            x = fwd()
-            e1.record()
-            loss = ((x - gt).abs() ** 2).sum()
-            e3 = torch.cuda.Event(enable_timing=True)
-            e3.record()
-            loss.backward()
-            e2.record()
-            torch.cuda.synchronize()
-            tf += e0.elapsed_time(e1)
-            tb += e3.elapsed_time(e2)
-        tf /= args.steps
-        tb /= args.steps
-        out.update({"metric": "unrolled FGP backward/forward time ratio (8 x 1024^2, 50 iterations, ckpt 10)",
-                    "value": tb / tf, "unit": "ratio", "higher_is_better": False, "forward_ms": tf,
-                    "backward_ms": tb, "forward_gpx_it_s": Bn * m * n * K / (tf * 1e-3) / 1e9})
+        out.update(measure_backward(ctv, dev, args.steps, args.warmup, args.config if args.config >= 0 else -1))
     print(json.dumps(out))
 
 

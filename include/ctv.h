@@ -52,8 +52,8 @@ typedef enum {
   CTV_EINVAL = 1,      /* invalid argument; nothing was launched */
   CTV_ENOMEM = 2,      /* a plan could not allocate its device memory */
   CTV_ECUDA = 3,       /* a CUDA runtime or cuFFT call failed */
-  CTV_ETIMEOUT = 4,    /* reserved: a bounded device wait ran out */
-  CTV_ENONFINITE = 5,  /* reserved: non-finite input detected */
+  CTV_ETIMEOUT = 4,    /* unused: no kernel of this library waits on the device */
+  CTV_ENONFINITE = 5,  /* a NaN or infinity in an input image (asynchronous, see below) */
   CTV_EUNSUPPORTED = 6, /* valid request that this build does not implement */
   CTV_ETOOBIG = 7       /* image larger than the fixed scratch of ctv_denoise_noalloc */
 } ctv_status;
@@ -110,7 +110,10 @@ typedef struct {
 
 /* Result statistics of one image. iters: iterations actually run; stopped:
  * 1 if the gap test stopped the run; primal, dual, gap: P(x_K), the dual value
- * of App. A (Eq. (30) times lambda) at q_K, and their difference. */
+ * of App. A (Eq. (30) times lambda) at q_K, and their difference; status:
+ * CTV_OK, CTV_ENONFINITE if b holds a NaN or an infinity (x and the values above
+ * are then not meaningful), or CTV_EINVAL for a negative or NaN lambda read from
+ * a device array. */
 typedef struct {
   int iters;
   int stopped;
@@ -122,6 +125,20 @@ typedef struct {
 
 const char* ctv_status_string(int status);
 int ctv_abi_version(void);
+
+/* Asynchronous errors. Problem (1) and (24) are defined for finite data; a NaN
+ * or an infinity in an input (b of a denoising call or plan, or z, sqrt_y or H
+ * of phase retrieval) is only seen on the device, after the call has returned.
+ * The kernels that read b (the finalize and the duality-gap evaluations of every
+ * solve) and the residual kernel of phase retrieval test each value as they load
+ * it and record CTV_ENONFINITE in a status word on the device; calls that return
+ * statistics also report it in ctv_stats.status. ctv_get_last_error synchronises
+ * `stream`, then returns the first error recorded on the current device since
+ * the previous ctv_get_last_error (CTV_OK if none) and clears it. The word is
+ * per device, shared by all streams: an error raised by work still running on
+ * another stream may be reported by a later call instead. CTV_ECUDA if the
+ * synchronisation or the read fails. */
+int ctv_get_last_error(ctv_stream stream);
 
 /* Kernel configurations of the fused FGP pass: iterations per pass (temporal
  * blocking depth) and the shared-memory region of one thread block. */
@@ -187,12 +204,13 @@ int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
  * arguments as ctv_denoise minus the dual state and the workspace: its scratch
  * (statistics record and FGP dual buffers) is a fixed device array inside the
  * library, sized for images of at most CTV_NOALLOC_MAX_PIXELS pixels (m * n;
- * 16 MiB, held on every GPU that loads the library until the process exits).
- * Larger images return CTV_ETOOBIG; opts->warm_start must be 0. It never calls
- * cudaMalloc, cudaFree or any allocating routine.
- * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ * 16 MiB, held on each device where the library's module has been loaded, until
+ * that device's context is destroyed). Larger images return CTV_ETOOBIG;
+ * opts->warm_start must be 0. It never calls cudaMalloc, cudaFree or any
+ * allocating routine.
+ * - Every call looks up the array's device address (cudaGetSymbolAddress) with
+ *   the caller's device current. The first call on a device loads the module
+ *   and places the array there; make that first call before any stream capture.
  * - Every call uses the same array, which keeps the previous call's contents
  *   (each call clears what must start at zero). Calls that overlap on the GPU -
  *   on two streams, or from two host threads - race on it and give wrong
@@ -325,12 +343,16 @@ int ctv_prox_grad_step(const void* z, const void* grad, float gamma, float tau,
                        ctv_stream stream);
 
 /* --------------------------------------------------------------------------
- * Measurement (no counterpart in the paper). ctv_profile_enable(1) resets the
- * counters and brackets every following launch of the fused FGP pass kernel
- * with CUDA events on its stream; ctv_profile_read synchronises on those events
- * and returns the summed kernel time in ms, the number of timed launches, the
- * pixel-iterations they processed, and the number of kernel launches of the
- * library since the last enable (counted whether or not timing is on).
+ * Measurement (no counterpart in the paper). ctv_profile_enable(on) resets the
+ * counters; on = 1 brackets every following launch of the fused FGP pass kernel
+ * with CUDA events on its stream, on = 2 brackets each run of consecutive pass
+ * launches of a single-image or equally sized batch solve (a run ends at a gap
+ * check or at the finalize), which leaves the overlap of back-to-back passes
+ * intact; on = 0 stops timing. ctv_profile_read synchronises on those events
+ * and returns the summed time in ms, the number of pass launches inside the
+ * timed intervals, the pixel-iterations they processed, and the number of
+ * kernel launches of the library since the last enable (counted whether or not
+ * timing is on).
  * -------------------------------------------------------------------------- */
 int ctv_profile_enable(int on);
 int ctv_profile_read(double* pass_ms, long long* pass_launches, double* pass_pixel_iters,

@@ -7,9 +7,9 @@ package does not load the library; the first call does, and fails loudly if it
 has not been built.
 """
 from .api import (TV_TYPES, Constraint, NO_CONSTRAINT, configs, ctv_denoise, ctv_denoise_batched,  # noqa: F401
-                  denoise, make_opts, workspace, PRPlan, Plan, ctv_prox_grad_step,
+                  denoise, get_last_error, make_opts, workspace, PRPlan, Plan, ctv_prox_grad_step,
                   UnrolledFGP, denoise_unrolled)
 
 __all__ = ["TV_TYPES", "Constraint", "NO_CONSTRAINT", "configs", "ctv_denoise", "ctv_denoise_batched",
-           "denoise", "make_opts", "workspace", "PRPlan", "Plan", "ctv_prox_grad_step",
+           "denoise", "get_last_error", "make_opts", "workspace", "PRPlan", "Plan", "ctv_prox_grad_step",
            "UnrolledFGP", "denoise_unrolled"]

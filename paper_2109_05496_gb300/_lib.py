@@ -51,6 +51,7 @@ P = C.POINTER
 SIGNATURES = {
     "ctv_status_string": (C.c_char_p, [c_int]),
     "ctv_abi_version": (c_int, []),
+    "ctv_get_last_error": (c_int, [c_void_p]),
     "ctv_num_configs": (c_int, []),
     "ctv_default_config": (c_int, [c_int, c_int, c_int, c_int]),
     "ctv_config_info": (c_int, [c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),

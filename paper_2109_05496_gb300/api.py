@@ -85,6 +85,13 @@ def _check_image(t: torch.Tensor, name: str, ndim: int):
         raise ValueError("%s must be %d-D with unit column stride" % (name, ndim))
 
 
+def get_last_error(stream=None) -> int:
+    """The C call ``ctv_get_last_error``: synchronises the stream and returns (and
+    clears) the first asynchronous error recorded on the current device, e.g.
+    CTV_ENONFINITE (5) for a NaN or infinity in an input image; 0 if none."""
+    return int(L.load().ctv_get_last_error(_stream_ptr(stream)))
+
+
 def workspace(batch: int, m: int, n: int, device) -> torch.Tensor:
     lib = L.load()
     nbytes = lib.ctv_denoise_workspace_size(batch, m, n)

@@ -36,7 +36,8 @@ struct DevStats {
   int stop_set;             // dual buffer set holding q at the stop
   int stop_iter;            // iteration at which the run stopped
   int iters;                // iterations represented by the last evaluation
-  int status;
+  int status;               // ctv_status of the image (CTV_ENONFINITE, CTV_EINVAL for a bad lambda)
+  unsigned int nonfinite;   // nonzero once an evaluation met a NaN or infinity in b
   double primal, dual, gap; // last evaluation
 };
 

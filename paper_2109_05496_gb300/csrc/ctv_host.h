@@ -41,12 +41,21 @@ int size_class(int m, int n);
 int num_configs();
 bool config_info(int i, int* T, int* RW, int* RH, int* NT);
 
+// Readers of the asynchronous error word of the units whose kernels test their
+// inputs (async_status.cuh): return the first recorded ctv_status code on the
+// current device (0: none) and clear it; -1 if the word cannot be read.
+int take_async_status_denoise();
+int take_async_status_plan();
+int take_async_status_pr();
+
 // Measurement hooks (prof.cu): count every launch; time fused passes when enabled.
 void count_launch();
 void count_launches(int n);
-// whether ctv_profile_enable(1) is in force (pass launches are then bracketed by events)
+// whether ctv_profile_enable(1 or 2) is in force (pass launches are then bracketed by events)
 bool prof_active();
+// 0 off, 1 every pass launch timed, 2 every run of consecutive pass launches timed
+int prof_mode();
 int prof_begin(cudaStream_t s);
-void prof_end(int slot, cudaStream_t s, double units);
+void prof_end(int slot, cudaStream_t s, double units, int launches);
 
 }  // namespace ctv

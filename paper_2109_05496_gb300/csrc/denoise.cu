@@ -19,6 +19,7 @@
 #include <utility>
 #include <vector>
 
+#include "async_status.cuh"
 #include "ctv.h"
 #include "ctv_configs.cuh"
 #include "ctv_device.cuh"
@@ -60,14 +61,17 @@ __global__ void __launch_bounds__(GAP_NT, 6) fgp_gap_kernel(GapParams p) {
   // blocks loop over the image's tiles (few blocks, so that a launch after the
   // stop costs little and the FP64 atomics stay few)
   double acc[3] = {0.0, 0.0, 0.0};
+  bool nf = false;
   const int tx = (p.n + GAP_RW - 3) / (GAP_RW - 2), ty = (p.m + GAP_RH - 3) / (GAP_RH - 2);
   for (int t = blockIdx.x; t < tx * ty; t += gridDim.x) {
     const int by = t / tx, bx = t - by * tx;
-    gap_tile_add<TV>(g, by * (GAP_RH - 2), bx * (GAP_RW - 2), qs, xs, acc);
+    gap_tile_add<TV>(g, by * (GAP_RH - 2), bx * (GAP_RW - 2), qs, xs, acc, nf);
     __syncthreads();
   }
+  const bool block_nf = __syncthreads_or(nf) != 0;
+  if (block_nf && threadIdx.x == 0) raise_async(CTV_ENONFINITE);
   block_sum<GAP_NT, 3>(acc, red);
-  gap_commit(st, acc, gridDim.x, 1u, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last);
+  gap_commit(st, acc, gridDim.x, 1u, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last, block_nf);
   // inside a stop graph, the check that stops the solve skips the remaining intervals
   if (p.n_cond > 0 && threadIdx.x == 0 && last && st->stop)
     for (int i = 0; i < p.n_cond; ++i) cudaGraphSetConditional(p.cond[i], 0u);
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(FIN_NT) fgp_finalize_kernel(GapParams p) {
   float4* qe = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
   const float lv = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
   const float lam = lv >= 0.f ? lv : 0.f;
+  bool nf = false;
   for (int j = blockIdx.y; j < m; j += gridDim.y) {
     const long long o = (long long)j * n + k;
     float4 qc = z4, qu = z4, ql = z4;
@@ -125,10 +130,20 @@ __global__ void __launch_bounds__(FIN_NT) fgp_finalize_kernel(GapParams p) {
       if (k > 0) ql = __ldg(q + o - 1);
     }
     const float2 bb = __ldg(b + (long long)j * p.ld + k);
+    nf |= nonfinite2(bb);
     x[(long long)j * p.ld + k] =
         proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)), j, k,
                p.C);
     if (qe != nullptr) qe[o] = qc;
+  }
+  // a NaN or infinity in b: one report per warp (the threads past column n have returned)
+  const unsigned am = __activemask();
+  if (__any_sync(am, nf) && (int)(threadIdx.x & 31) == __ffs(am) - 1) {
+    raise_async(CTV_ENONFINITE);
+    if (p.st != nullptr) {
+      atomicOr(&p.st[z].nonfinite, 1u);
+      atomicExch(&p.st[z].status, (int)CTV_ENONFINITE);
+    }
   }
 }
 
@@ -137,6 +152,8 @@ cudaError_t launch_finalize(const GapParams& p, int batch, cudaStream_t s) {
   fgp_finalize_kernel<<<grid, FIN_NT, 0, s>>>(p);
   return cudaGetLastError();
 }
+
+int take_async_status_denoise() { return take_unit_async_status(); }
 
 int sm_count() {
   static int n = 0;
@@ -514,6 +531,16 @@ ctv_status run_denoise(const DenoiseCall& c) {
       const float4* q_in = (const float4*)c.dual_state;
       const float4* r_in = (const float4*)c.dual_state;
       bool first = !warm;
+      // measurement: mode 1 times every pass, mode 2 each run of passes up to a check
+      const int pmode = sg == nullptr ? prof_mode() : 0;
+      int run_slot = -1, run_n = 0;
+      double run_units = 0.0;
+      auto close_run = [&](cudaStream_t rs) {
+        if (run_slot >= 0) prof_end(run_slot, rs, run_units, run_n);
+        run_slot = -1;
+        run_n = 0;
+        run_units = 0.0;
+      };
       while (k <= K) {
         if (sg != nullptr && !sg->open) {
           es = sg->open_interval();
@@ -532,11 +559,15 @@ ctv_status run_denoise(const DenoiseCall& c) {
         p.r_in = r_in;
         p.q_out = set_q[out];
         p.r_out = set_r[out];
-        const int slot = sg == nullptr ? prof_begin(es) : -1;
+        const double units = (double)c.batch * (double)px * (double)steps;
+        const int slot = pmode == 1 ? prof_begin(es) : -1;
+        if (pmode == 2 && run_slot < 0) run_slot = prof_begin(es);
         if (launch_pass(c.tv, cfg, p, grid, es) != cudaSuccess) return CTV_ECUDA;
         count_launch();
         if (sg != nullptr) sg->kernels++;
-        prof_end(slot, es, (double)c.batch * (double)px * (double)steps);
+        prof_end(slot, es, units, 1);
+        run_units += units;
+        ++run_n;
         first = false;
         k += steps;
         last_set = out;
@@ -544,6 +575,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
         r_in = set_r[out];
         out ^= 1;
         if (check_every > 0 && (k - 1) % check_every == 0 && k - 1 < K) {
+          close_run(es);
           gg.default_set = last_set;
           gg.zero_q = 0;
           gg.x = nullptr;
@@ -560,6 +592,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
           }
         }
       }
+      close_run(es);
       if (sg != nullptr && sg->open && !sg->close_interval()) return CTV_ECUDA;
     }
     // finalize: x = P_C(b - lam L^T q_K), final statistics, optional export of q_K

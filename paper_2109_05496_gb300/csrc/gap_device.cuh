@@ -3,6 +3,7 @@
 // reduced in FP64.
 #pragma once
 
+#include "async_status.cuh"
 #include "ctv_device.cuh"
 
 namespace ctv {
@@ -29,10 +30,11 @@ constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
 //   acc[0] = ||x - b||^2, acc[1] = TV(x), acc[2] = ||b||^2 - ||w||^2 + ||w - P_C(w)||^2
 // (w = b - lam L^T q), i.e. 2 P - 2 lam TV and 2 D of App. A.
 // gap_tile_add adds this thread's share of the three sums into acc (no block
-// reduction; the caller synchronises before reusing qs and xs).
+// reduction; the caller synchronises before reusing qs and xs) and sets nf when
+// one of the thread's values of b is a NaN or an infinity.
 template <int TV>
 __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, float4* qs, float2* xs,
-                                             double (&acc)[3]) {
+                                             double (&acc)[3], bool& nf) {
   constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
   const int m = g.m, n = g.n;
   const int gj0 = j0 - 1, gk0 = k0 - 1;
@@ -51,6 +53,7 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
     if ((unsigned)gj < (unsigned)m && (unsigned)gk < (unsigned)n) {
       if (g.q != nullptr) v = __ldg(g.q + (long long)gj * n + gk);
       bv[s] = __ldg(g.b + (long long)gj * g.ld + gk);
+      nf |= nonfinite2(bv[s]);
     }
     qs[i] = v;
   }
@@ -105,22 +108,16 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
   acc[2] += (double)fa2;
 }
 
-template <int TV>
-__device__ __forceinline__ void gap_tile(const GapImg& g, int j0, int k0, float4* qs, float2* xs, double* red,
-                                         double (&acc)[3]) {
-  acc[0] = acc[1] = acc[2] = 0.0;
-  gap_tile_add<TV>(g, j0, k0, qs, xs, acc);
-  block_sum<GAP_NT, 3>(acc, red);
-}
-
 // Adds the block sums into st and lets the commit that completes the reduction
 // (nblk units in all; this one covers `units` of them) turn them into primal,
 // dual and gap, apply the stopping test (checks) or record the final iteration
-// count, and reset the accumulators. Thread 0 holds the block sums.
+// count, and reset the accumulators. Thread 0 holds the block sums; nonfinite
+// (any thread's flag, block-reduced by the caller) marks the image's record.
 __device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3], unsigned nblk, unsigned units,
                                            float lam, bool bad_lam, int set, int stopped, int iter, double gap_tol,
-                                           int final_call, int* last) {
+                                           int final_call, int* last, bool nonfinite) {
   if (threadIdx.x == 0) {
+    if (nonfinite) atomicOr(&st->nonfinite, 1u);
     atomicAdd(&st->acc[0], acc[0]);
     atomicAdd(&st->acc[1], acc[1]);
     atomicAdd(&st->acc[2], acc[2]);
@@ -138,6 +135,7 @@ __device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3],
     st->dual = D;
     st->gap = P - D;
     if (bad_lam) st->status = 1;   // CTV_EINVAL
+    if (*(volatile unsigned int*)&st->nonfinite) st->status = 5;   // CTV_ENONFINITE
     if (!final_call) {
       st->iters = iter;
       if (gap_tol > 0.0 && P - D <= gap_tol * fmax(P, 1e-30)) {

@@ -9,14 +9,17 @@
 // ping-pong dual buffer sets of the FGP passes) in the file-scope device array
 // below, of a fixed size chosen for images of up to CTV_NOALLOC_MAX_PIXELS pixels.
 //
-// The array lives in every GPU that loads this library, for as long as the
-// library stays loaded. Host code only holds a stand-in symbol for it, so its
-// device address is looked up once per device with cudaGetSymbolAddress (on the
-// first call made with that device current) and passed to the kernels.
+// The array is placed on a device when the library's module is loaded there
+// and stays until that device's context is destroyed. Host code only holds a
+// stand-in symbol for it, so every call looks up the array's device address with
+// cudaGetSymbolAddress, with the caller's device current, and passes it to the
+// kernels. The lookup allocates nothing and, once the module is loaded, is cheap;
+// doing it on every call (rather than caching it) keeps the address right after a
+// cudaDeviceReset or under another context, where the module is loaded again and
+// the array can move. The first call on a device loads the module (and places
+// the array), so it must come before any stream capture.
 #include <cuda_runtime.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "ctv.h"
 #include "ctv_device.cuh"
@@ -29,21 +32,11 @@ constexpr size_t kNoAllocScratchBytes = 256 + 4 * sizeof(float4) * (size_t)CTV_N
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Device address of g_noalloc_scratch in the current context.
 ctv_status scratch_for_current_device(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CTV_ECUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return CTV_ECUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return CTV_ECUDA;
+  *out = p;
   return CTV_OK;
 }
 

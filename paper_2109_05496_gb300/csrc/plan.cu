@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "async_status.cuh"
 #include "ctv.h"
 #include "ctv_configs.cuh"
 #include "ctv_device.cuh"
@@ -105,10 +106,13 @@ struct ListGapParams {
 
 __device__ __forceinline__ void list_gap_commit(const PlanImg* d, double (&acc)[3], double* red, unsigned units,
                                                 int set, int stopped, int iter, double gap_tol, int final_call,
-                                                int* last) {
+                                                int* last, bool& nf) {
+  const bool block_nf = __syncthreads_or(nf) != 0;
+  if (block_nf && threadIdx.x == 0) raise_async(CTV_ENONFINITE);
   block_sum<GAP_NT, 3>(acc, red);
-  gap_commit(d->st, acc, d->gnblk, units, d->lam, false, set, stopped, iter, gap_tol, final_call, last);
+  gap_commit(d->st, acc, d->gnblk, units, d->lam, false, set, stopped, iter, gap_tol, final_call, last, block_nf);
   acc[0] = acc[1] = acc[2] = 0.0;
+  nf = false;
 }
 
 // Persistent: each block walks a contiguous run of gap tiles (items are in
@@ -124,12 +128,14 @@ __global__ void __launch_bounds__(GAP_NT, 4) fgp_gap_list_kernel(ListGapParams p
   const int per = (p.n_items + (int)gridDim.x - 1) / (int)gridDim.x;
   const int i0 = (int)blockIdx.x * per, i1 = min(i0 + per, p.n_items);
   double acc[3] = {0.0, 0.0, 0.0};
+  bool nf = false;
   int cur = -1, cur_set = 0, cur_stopped = 0;
   unsigned units = 0;
   for (int i = i0; i < i1; ++i) {
     const WorkItem w = p.items[i];
     if (w.img != cur && units > 0) {
-      list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last);
+      list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last,
+                      nf);
       units = 0;
     }
     cur = w.img;
@@ -154,17 +160,20 @@ __global__ void __launch_bounds__(GAP_NT, 4) fgp_gap_list_kernel(ListGapParams p
     g.C = d.C;
     const int j0 = (w.tile / d.gtiles_x) * (GAP_RH - 2), k0 = (w.tile % d.gtiles_x) * (GAP_RW - 2);
     switch (d.tv) {
-      case TV1_ISO: gap_tile_add<TV1_ISO>(g, j0, k0, qs, xs, acc); break;
-      case TV1_ANISO: gap_tile_add<TV1_ANISO>(g, j0, k0, qs, xs, acc); break;
-      case TV2_ISO: gap_tile_add<TV2_ISO>(g, j0, k0, qs, xs, acc); break;
-      default: gap_tile_add<TV2_ANISO>(g, j0, k0, qs, xs, acc); break;
+      case TV1_ISO: gap_tile_add<TV1_ISO>(g, j0, k0, qs, xs, acc, nf); break;
+      case TV1_ANISO: gap_tile_add<TV1_ANISO>(g, j0, k0, qs, xs, acc, nf); break;
+      case TV2_ISO: gap_tile_add<TV2_ISO>(g, j0, k0, qs, xs, acc, nf); break;
+      default: gap_tile_add<TV2_ANISO>(g, j0, k0, qs, xs, acc, nf); break;
     }
     __syncthreads();   // qs and xs are reused by the next tile
     ++units;
   }
   if (units > 0)
-    list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last);
+    list_gap_commit(p.imgs + cur, acc, red, units, cur_set, cur_stopped, p.iter, p.gap_tol, p.final_call, &last,
+                      nf);
 }
+
+int take_async_status_plan() { return take_unit_async_status(); }
 
 // Blocks of a gap / finalize launch: resident blocks, at most one per item.
 static int gap_list_blocks(int n_items) {

@@ -21,6 +21,7 @@
 
 #include <vector>
 
+#include "async_status.cuh"
 #include "ctv_device.cuh"
 #include "ctv_host.h"
 
@@ -55,17 +56,21 @@ __global__ void __launch_bounds__(PR_NT) pr_residual(const float2* __restrict__ 
   __shared__ double red[PR_NT / 32];
   const int j = blockIdx.y, k = blockIdx.x * PR_NT + threadIdx.x;
   double l = 0.0;
+  bool nf = false;
   if (k < n) {
     const float2 f = F[(long long)j * ldF + k];
     const float xr = f.x * inv_mn, xi = f.y * inv_mn;
     const float a = sqrtf(xr * xr + xi * xi);
     const float sy = __ldg(sqrt_y + (long long)j * ldy + k);
+    // a NaN or infinity in z, H or sqrt(y) reaches this point as a non-finite field or amplitude
+    nf = !(isfinite(a) && isfinite(sy));
     const float d = a - sy;
     float ur = 1.f, ui = 0.f;
     if (a > 0.f) { ur = xr / a; ui = xi / a; }
     Q[(long long)j * ldQ + k] = make_float2(ur * d, ui * d);
     l = 0.5 * (double)d * (double)d;
   }
+  if (__any_sync(0xffffffffu, nf) && (threadIdx.x & 31) == 0) raise_async(CTV_ENONFINITE);
   if (loss == nullptr) return;
   double v[1] = {l};
   __syncthreads();
@@ -132,6 +137,8 @@ __global__ void __launch_bounds__(PR_NT) pr_ls_terms(const float2* __restrict__ 
 }
 
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int take_async_status_pr() { return take_unit_async_status(); }
 
 }  // namespace ctv
 

@@ -1,9 +1,12 @@
 // Kernel-level timing of the fused FGP pass with CUDA events, for measurement.
 //
-// While enabled, every launch of the fused pass kernel is bracketed by two
-// events recorded on the launching stream; ctv_profile_read sums their elapsed
-// times. Every kernel launch of the library is counted whether or not timing
-// is enabled.
+// Mode 1 brackets every launch of the fused pass kernel with two events recorded
+// on the launching stream. Mode 2 brackets each run of consecutive pass launches
+// of a solve instead (closed before a gap check or the finalize), so that the
+// passes inside a run keep their back-to-back overlap (programmatic dependent
+// launch) and the time is that of the pass sequence itself. ctv_profile_read
+// sums the bracketed times. Every kernel launch of the library is counted
+// whether or not timing is enabled.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -17,10 +20,11 @@ namespace ctv {
 
 namespace {
 std::mutex g_mu;
-bool g_on = false;
+int g_mode = 0;                  // 0 off, 1 per launch, 2 per run of consecutive passes
 std::vector<cudaEvent_t> g_ev;   // pairs (start, stop)
 size_t g_used = 0;               // pairs in use
 double g_units = 0.0;            // pixel-iterations of the timed launches
+long long g_timed = 0;           // pass launches inside the bracketed intervals
 std::atomic<long long> g_launches{0};
 long long g_launch_base = 0;
 }  // namespace
@@ -29,12 +33,17 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 bool prof_active() {
   std::lock_guard<std::mutex> lk(g_mu);
-  return g_on;
+  return g_mode != 0;
+}
+
+int prof_mode() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_mode;
 }
 
 int prof_begin(cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on) return -1;
+  if (g_mode == 0) return -1;
   if (g_used * 2 + 2 > g_ev.size()) {
     for (int i = 0; i < 2; ++i) {
       cudaEvent_t e;
@@ -47,11 +56,12 @@ int prof_begin(cudaStream_t s) {
   return slot;
 }
 
-void prof_end(int slot, cudaStream_t s, double units) {
+void prof_end(int slot, cudaStream_t s, double units, int launches) {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEventRecord(g_ev[2 * slot + 1], s);
   g_units += units;
+  g_timed += launches;
 }
 
 }  // namespace ctv
@@ -59,10 +69,12 @@ void prof_end(int slot, cudaStream_t s, double units) {
 extern "C" {
 
 int ctv_profile_enable(int on) {
+  if (on < 0 || on > 2) return CTV_EINVAL;
   std::lock_guard<std::mutex> lk(ctv::g_mu);
-  ctv::g_on = on != 0;
+  ctv::g_mode = on;
   ctv::g_used = 0;
   ctv::g_units = 0.0;
+  ctv::g_timed = 0;
   ctv::g_launch_base = ctv::g_launches.load();
   return CTV_OK;
 }
@@ -77,7 +89,7 @@ int ctv_profile_read(double* pass_ms, long long* pass_launches, double* pass_pix
     total += ms;
   }
   if (pass_ms) *pass_ms = total;
-  if (pass_launches) *pass_launches = (long long)ctv::g_used;
+  if (pass_launches) *pass_launches = ctv::g_timed;
   if (pass_pixel_iters) *pass_pixel_iters = ctv::g_units;
   if (all_launches) *all_launches = ctv::g_launches.load() - ctv::g_launch_base;
   return CTV_OK;

@@ -52,3 +52,23 @@ def run_oracle(b_c64: np.ndarray, lam: float, K: int, tv: str, alpha: float, C, 
 def objective(x_c: np.ndarray, b, lam, tv, alpha) -> float:
     xt = torch.as_tensor(np.asarray(x_c).astype(np.complex128))
     return float(primal_value((xt.real.clone(), xt.imag.clone()), b, f32(lam), tv, f32(alpha)))
+
+
+def _oracle_x_job(args):
+    """x_K of the oracle for one image (a process-pool job)."""
+    b_c64, lam, K, tv, alpha, amp_max = args
+    torch.set_num_threads(1)
+    _, res = run_oracle(b_c64, lam, K, tv, alpha, oracle_constraint(amp_max))
+    return (res.x[0] + 1j * res.x[1]).numpy()
+
+
+def oracle_x_many(jobs, workers: int = 0):
+    """The oracle's x_K for many small images, (b_c64, lam, K, tv, alpha, amp_max)
+    each, in a pool of spawned processes (a forked child of a process that has
+    used the GPU is not safe; spawned ones start clean)."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_oracle_x_job, jobs, chunksize=2))

@@ -96,7 +96,8 @@ def test_unrolled_forward_equals_batched_denoise():
         assert torch.equal(x1, x2)
 
 
-def test_finite_differences_fp64_32x32():
+@pytest.mark.parametrize("tv", TV_NAMES)
+def test_finite_differences_fp64_32x32(tv):
     # FP64 central differences of the oracle's loss ||x - x_gt||^2 along random
     # directions against the GPU gradient (the gradient of the same loss)
     m = n = 32
@@ -108,12 +109,12 @@ def test_finite_differences_fp64_32x32():
     Co = oracle_constraint(1.0)
 
     def loss64(bc, lamv):
-        res = fgp((bc.real.clone(), bc.imag.clone()), lamv, K, "tv1_iso", 0.5, Co)
+        res = fgp((bc.real.clone(), bc.imag.clone()), lamv, K, tv, 0.5, Co)
         return float(((res.x[0] - gt.real) ** 2).sum() + ((res.x[1] - gt.imag) ** 2).sum())
 
     b = torch.from_numpy(b_np).cuda().requires_grad_(True)
     lt = torch.tensor([lam], dtype=torch.float32, device="cuda", requires_grad=True)
-    x = ctv.denoise_unrolled(b, lt, "tv1_iso", K, ctv.Constraint(amp_max=1.0), 0.5, 5)
+    x = ctv.denoise_unrolled(b, lt, tv, K, ctv.Constraint(amp_max=1.0), 0.5, 5)
     g = torch.from_numpy(clean.astype(np.complex64)).cuda()[None]
     loss = ((x - g).abs() ** 2).sum()
     loss.backward()
@@ -151,3 +152,44 @@ def test_full_size_gradient_window():
         want = ob[0, j - j0, k - k0]
         scale = np.abs(ob).max()
         assert abs(gb[i, j, k] - want) <= 2e-3 * scale
+
+
+def _oracle_forward_derivative(b_np, lam, K, tv, alpha, Co, xbar_np, db=None):
+    """d<xbar, x_K>/dlam (db None) or the derivative along the input direction db,
+    by forward-mode FP64 differentiation of the oracle (one pass, no stored graph)."""
+    import torch.autograd.forward_ad as fwAD
+    bb = torch.tensor(b_np.astype(np.complex128))
+    xb = torch.tensor(xbar_np.astype(np.complex128))
+    with fwAD.dual_level():
+        if db is None:
+            lam_d = fwAD.make_dual(torch.tensor(f32(lam), dtype=DT), torch.tensor(1.0, dtype=DT))
+            b_pair = (bb.real.clone(), bb.imag.clone())
+        else:
+            lam_d = f32(lam)
+            d = torch.tensor(db)
+            b_pair = (fwAD.make_dual(bb.real.clone(), d.real.clone()), fwAD.make_dual(bb.imag.clone(), d.imag.clone()))
+        res = fgp(b_pair, lam_d, K, tv, f32(alpha), Co)
+        loss = (res.x[0] * xb.real).sum() + (res.x[1] * xb.imag).sum()
+        return float(fwAD.unpack_dual(loss).tangent)
+
+
+def test_full_size_lambda_gradient_and_directional_derivative():
+    # The differentiation workload (8 x 1024^2, 50 iterations, checkpoints every
+    # 10): lambda-bar of two whole images, and <b-bar, d> along a random input
+    # direction d, against forward-mode FP64 derivatives of the oracle's unrolled
+    # Algorithm 2 on the full image (an independent differentiation mode: no
+    # reverse sweep, no checkpoints).
+    Bn, m, n, K = 8, 1024, 1024, 50
+    imgs = np.stack([to_c64(noisy_phantom(m, n, 0.1, seed=600 + i)[1]) for i in range(Bn)])
+    rng = np.random.default_rng(9)
+    xbar = (rng.standard_normal((Bn, m, n)) + 1j * rng.standard_normal((Bn, m, n))).astype(np.complex64)
+    lams = np.linspace(0.02, 0.09, Bn)
+    C, Co = ctv.Constraint(amp_max=1.0), oracle_constraint(1.0)
+    _, gb, gl = gpu_grads(imgs, lams, K, "tv1_iso", 0.5, C, xbar, 10)
+    for i in (1, 6):
+        want = _oracle_forward_derivative(imgs[i], lams[i], K, "tv1_iso", 0.5, Co, xbar[i])
+        assert abs(gl[i] - want) <= 2e-3 * abs(want), (gl[i], want)
+        d = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+        want_b = _oracle_forward_derivative(imgs[i], lams[i], K, "tv1_iso", 0.5, Co, xbar[i], db=d)
+        got_b = float((gb[i].real.astype(np.float64) * d.real + gb[i].imag.astype(np.float64) * d.imag).sum())
+        assert abs(got_b - want_b) <= 2e-3 * abs(want_b), (got_b, want_b)

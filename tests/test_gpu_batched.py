@@ -133,6 +133,36 @@ def test_plan_full_workload_sampled():
         assert torch.equal(x1, ims[i]["x"])
 
 
+def test_plan_full_workload_oracle_subset():
+    # The 512-image workload against the oracle: every image of at most 256^2
+    # pixels and 32 seeded random larger ones, element by element after 100
+    # iterations, with the objective bar of the single-image tests.
+    from tests.helpers import objective, oracle_x_many
+    from tests.test_gpu_denoise import OBJTOL, XTOL
+    shapes, lams, types, imgs = make_batch(512, 64, 1024, seed=2021)
+    ims = plan_images(imgs, lams, types)
+    plan = ctv.Plan(ims, 100)
+    plan.execute()
+    torch.cuda.synchronize()
+    px = np.array([m * n for m, n in shapes])
+    small = [i for i in range(len(shapes)) if px[i] <= 256 * 256]
+    rng = np.random.default_rng(77)
+    large = sorted(rng.choice([i for i in range(len(shapes)) if px[i] > 256 * 256], 32, replace=False).tolist())
+    picked = small + large
+    assert len(small) > 100
+    jobs = [(imgs[i], float(lams[i]), 100, TV_NAMES[int(types[i])], 0.5, 1.0) for i in picked]
+    xo_all = oracle_x_many(jobs)
+    for i, xo in zip(picked, xo_all):
+        tv = TV_NAMES[int(types[i])]
+        xg = ims[i]["x"].cpu().numpy()
+        binf = float(np.abs(imgs[i]).max())
+        assert float(np.abs(xg.astype(np.complex128) - xo).max()) <= XTOL * binf, i
+        bt = torch.as_tensor(imgs[i].astype(np.complex128))
+        bp = (bt.real.clone(), bt.imag.clone())
+        Pg, Po = objective(xg, bp, lams[i], tv, 0.5), objective(xo, bp, lams[i], tv, 0.5)
+        assert abs(Pg - Po) <= OBJTOL * abs(Po), i
+
+
 def test_plan_rejects_unsupported_configuration():
     shapes, lams, types, imgs = make_batch(2, 20, 40, seed=3)
     with pytest.raises(RuntimeError):

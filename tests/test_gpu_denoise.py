@@ -243,6 +243,27 @@ def test_full_size_sampled(tv):
     assert st["primal"] == pytest.approx(P, rel=1e-6)
 
 
+# --------------------------------------------------------------- full size (2048^2, 200 iterations), whole image
+@pytest.mark.parametrize("tv", TV_NAMES)
+def test_full_size_whole_image(tv):
+    # The headline workload's solve (2048^2, amplitude bound plus support
+    # rectangle, 200 iterations) against the oracle on the whole image: every
+    # pixel within 1e-4 ||b||_inf and the objective within 1e-6, after the same
+    # iteration count; and the fused FP64 primal value against the oracle's
+    # evaluation of the GPU's x.
+    m = n = 2048
+    K = 200
+    lam = 0.05
+    _, noisy = noisy_phantom(m, n, 0.1, seed=2049)
+    rect = support_rect(m, n)
+    Cg = ctv.Constraint(amp_max=1.0, rect=rect)
+    x, st = gpu_denoise(noisy, lam, K, tv, 0.5, Cg)
+    bp, res = run_oracle(noisy, lam, K, tv, 0.5, oracle_constraint(1.0, rect=rect))
+    check_parity(x, res, bp, noisy, lam, tv, 0.5)
+    assert st["iters"] == K and st["status"] == 0
+    assert st["primal"] == pytest.approx(objective(x, bp, lam, tv, 0.5), rel=1e-6)
+
+
 # --------------------------------------------------------------- argument errors
 def test_invalid_arguments_raise():
     b = torch.zeros(8, 8, dtype=torch.complex64, device="cuda")

@@ -5,8 +5,10 @@ fixed array inside the library instead of a caller workspace.
 
 Checked through the C ABI against ctv_denoise on two calls in a row (different
 sizes, TV types and constraints, so stale scratch from the first call would
-show), within the parity tolerance of the other tests. This file is collected
-last on purpose."""
+show), within the parity tolerance of the other tests: once without a stopping
+test, once with a call that stops early followed by one that must run all its
+iterations (the stop flag lives in the shared array), and at the largest
+accepted size. This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -54,9 +56,41 @@ def test_noalloc_matches_ctv_denoise_twice():
         assert st.gap == pytest.approx(st_ref["gap"], rel=1e-4, abs=1e-9 * st_ref["primal"])
 
 
+def _compare(lib, m, n, lam, tv, C, K, seed, check_every=0, gap_tol=0.0):
+    _, noisy = noisy_phantom(m, n, 0.1, seed=seed)
+    b = torch.from_numpy(to_c64(noisy)).cuda()
+    x_ref, st_ref = ctv.denoise(b, lam, tv, K, C, 0.5, check_every=check_every, gap_tol=gap_tol,
+                                return_stats=True)
+    x = torch.empty_like(b)
+    opts = ctv.make_opts(K, check_every, gap_tol, 0.5)
+    st = _lib.CtvStats()
+    status = call_noalloc(lib, b, x, lam, C, tv, opts, st)
+    assert status == 0, lib.ctv_status_string(status)
+    torch.cuda.synchronize()
+    assert float((x - x_ref).abs().max()) <= XTOL * float(b.abs().max())
+    assert st.iters == st_ref["iters"] and bool(st.stopped) == st_ref["stopped"]
+    assert st.primal == pytest.approx(st_ref["primal"], rel=1e-6)
+    return st
+
+
+def test_noalloc_stop_does_not_carry_into_the_next_call():
+    lib = _lib.load()
+    C = ctv.Constraint(amp_max=1.0)
+    st = _compare(lib, 256, 256, 0.05, "tv1_iso", C, 200, 81, check_every=10, gap_tol=1e-4)
+    assert st.stopped and st.iters < 200
+    st = _compare(lib, 200, 180, 0.05, "tv1_aniso", C, 30, 82, check_every=10, gap_tol=0.0)
+    assert not st.stopped and st.iters == 30
+
+
+def test_noalloc_largest_accepted_size():
+    lib = _lib.load()
+    st = _compare(lib, 512, 512, 0.04, "tv2_iso", ctv.Constraint(amp_max=1.0, rect=support_rect(512, 512)), 24, 83)
+    assert st.iters == 24
+
+
 def test_noalloc_rejects_oversize_images():
     lib = _lib.load()
-    m, n = 1024, 1024        # more than CTV_NOALLOC_MAX_PIXELS = 512 * 512
+    m, n = 513, 512          # one row more than CTV_NOALLOC_MAX_PIXELS = 512 * 512
     b = torch.zeros(m, n, dtype=torch.complex64, device="cuda")
     x = torch.empty_like(b)
     st = _lib.CtvStats()
