@@ -154,9 +154,10 @@ int ctv_default_config(int m, int n, int iters, int tv_type);
  * start ignored), writes x, synchronises `stream`, returns the fastest
  * configuration in *best_config (times_ms: NULL or ctv_num_configs() floats) and
  * records it for the image's size class and TV type, which then becomes the
- * choice of every call with opts->config = -1. The size class of an m x n image
- * is floor(log2(m n)); ctv_tune_get / ctv_tune_set read and write that table
- * (-1: untuned) so that it can be saved and restored. */
+ * choice of every call with opts->config = -1 on the same device. The size class
+ * of an m x n image is floor(log2(m n)); ctv_tune_get / ctv_tune_set read and
+ * write that table (-1: untuned) so that it can be saved and restored. There is
+ * one table per device; every call uses the current device's. */
 int ctv_size_class(int m, int n);
 int ctv_tune_get(int size_class, int tv_type, int* config);
 int ctv_tune_set(int size_class, int tv_type, int config);

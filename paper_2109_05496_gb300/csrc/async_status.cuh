@@ -37,8 +37,4 @@ inline int take_unit_async_status() {
 }
 
 }  // namespace
-
-// Non-finite test of one complex input value (NaN or an infinity in either part).
-__device__ __forceinline__ bool nonfinite2(float2 v) { return !(isfinite(v.x) && isfinite(v.y)); }
-
 }  // namespace ctv

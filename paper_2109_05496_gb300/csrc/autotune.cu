@@ -21,14 +21,22 @@ namespace ctv {
 namespace {
 constexpr int kClasses = 40;
 std::mutex g_mu;
-int g_table[kClasses][4];   // -1: not tuned
+// one table per device ordinal (tuned choices are facts about one GPU); the last
+// slot serves devices with ordinals beyond the cached range
+int g_table[kMaxDevices + 1][kClasses][4];   // -1: not tuned
 bool g_init = false;
 
 void init_locked() {
   if (g_init) return;
-  for (int c = 0; c < kClasses; ++c)
-    for (int t = 0; t < 4; ++t) g_table[c][t] = -1;
+  for (int d = 0; d <= kMaxDevices; ++d)
+    for (int c = 0; c < kClasses; ++c)
+      for (int t = 0; t < 4; ++t) g_table[d][c][t] = -1;
   g_init = true;
+}
+
+int (&table_of_current_device())[kClasses][4] {
+  const int d = device_slot();
+  return g_table[d >= 0 ? d : kMaxDevices];
 }
 }  // namespace
 
@@ -42,7 +50,7 @@ int tuned_config(int m, int n, int tv) {
   std::lock_guard<std::mutex> lk(g_mu);
   init_locked();
   if (tv < 0 || tv > 3) return -1;
-  return g_table[size_class(m, n)][tv];
+  return table_of_current_device()[size_class(m, n)][tv];
 }
 
 }  // namespace ctv
@@ -55,7 +63,7 @@ int ctv_tune_set(int size_class, int tv_type, int config) {
   if (config < -1 || config >= num_configs()) return CTV_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
   init_locked();
-  g_table[size_class][tv_type] = config;
+  table_of_current_device()[size_class][tv_type] = config;
   return CTV_OK;
 }
 
@@ -64,7 +72,7 @@ int ctv_tune_get(int size_class, int tv_type, int* config) {
   if (config == nullptr || size_class < 0 || size_class >= kClasses || tv_type < 0 || tv_type > 3) return CTV_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
   init_locked();
-  *config = g_table[size_class][tv_type];
+  *config = table_of_current_device()[size_class][tv_type];
   return CTV_OK;
 }
 

@@ -271,13 +271,9 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
 template <int KIND, int TV, int T, int A, int B, int C, int CONS>
 static cudaError_t launch_hist_c(const PassParams& p, dim3 grid, float4* hist, long long plane, cudaStream_t s) {
   using G = CfgGeom<KIND, A, B, C>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_hist_pass_kernel<KIND, TV, T, A, B, C, CONS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static bool attr_done[kMaxDevices] = {};
+  cudaError_t e = smem_attr_once(fgp_hist_pass_kernel<KIND, TV, T, A, B, C, CONS>, G::SMEM, attr_done);
+  if (e != cudaSuccess) return e;
   fgp_hist_pass_kernel<KIND, TV, T, A, B, C, CONS><<<grid, G::NT, G::SMEM, s>>>(p, hist, plane);
   return cudaGetLastError();
 }
@@ -717,13 +713,9 @@ static cudaError_t launch_adj_stream_t(const AdjParams& p, int batch, cudaStream
   const int ncw = (p.n + ADJS_OWN - 1) / ADJS_OWN;
   dim3 grid((ncw + ADJS_WARPS - 1) / ADJS_WARPS, (p.m + ADJS_H - 1) / ADJS_H, batch);
   constexpr size_t smem = sizeof(AdjsSlot) * ADJS_D * ADJS_WARPS;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(adj_stream_kernel<TV, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static bool attr_done[kMaxDevices] = {};
+  cudaError_t e = smem_attr_once(adj_stream_kernel<TV, CONS>, smem, attr_done);
+  if (e != cudaSuccess) return e;
   adj_stream_kernel<TV, CONS><<<grid, 32 * ADJS_WARPS, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -743,13 +735,9 @@ static cudaError_t launch_adj2_t(const AdjParams& p, int batch, cudaStream_t s) 
   const int ncw = (p.n + ADJ2_OWN - 1) / ADJ2_OWN;
   dim3 grid((ncw + ADJS_WARPS - 1) / ADJS_WARPS, (p.m + ADJ2_H - 1) / ADJ2_H, batch);
   constexpr size_t smem = sizeof(Adj2Slot) * ADJ2_D * ADJS_WARPS;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(adj2_stream_kernel<TV, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static bool attr_done[kMaxDevices] = {};
+  cudaError_t e = smem_attr_once(adj2_stream_kernel<TV, CONS>, smem, attr_done);
+  if (e != cudaSuccess) return e;
   adj2_stream_kernel<TV, CONS><<<grid, 32 * ADJS_WARPS, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -38,6 +38,13 @@ struct CfgGeom {
   static constexpr int NT = KIND == 0 ? C : 32 * A * B;
   static constexpr size_t SMEM = KIND == 0 ? (size_t)RW * RH * (sizeof(float4) + sizeof(float2))
                                            : (size_t)RW * RH * 3 * sizeof(float2) + (size_t)B * RW * sizeof(float2);
+  // Resident blocks per SM the pass kernel is compiled for: one row per thread
+  // fits in 32 registers (two 1024-thread blocks per SM), up to four rows in 64
+  // (two 512-thread blocks); deeper strips need more registers and run one
+  // block (of their size) per SM.
+  static constexpr int MINB = KIND != 1 ? 1
+                              : C == 1 ? 65536 / (NT * 32)
+                              : (C <= 4 && NT <= 512) ? 65536 / (NT * 64) : 1;
 };
 
 template <int KIND, int TV, int T, int A, int B, int C, bool HIST = false, int CONS = CONS_GEN>

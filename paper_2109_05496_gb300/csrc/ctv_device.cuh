@@ -43,6 +43,9 @@ struct DevStats {
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 
+// Non-finite test of one complex input value (NaN or an infinity in either part).
+__device__ __forceinline__ bool nonfinite2(float2 v) { return !(isfinite(v.x) && isfinite(v.y)); }
+
 // P_C: support first (x = 0 outside), then the amplitude bound of Eq. (26),
 // x * amax / max{amax, |x|}, or the box on the real and imaginary parts.
 __device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev& c) {
@@ -344,13 +347,26 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
   // support rectangle, so their edge path needs no per-pixel image test in
   // the iterations; the general constraint (mask, box) keeps the tests.
   constexpr bool TESTS = EDGE && CONS == CONS_GEN;
-  for (int it = 0; it < nsteps; ++it) {
-    // Rows whose values can still reach the interior after the remaining steps:
-    // step it must produce q, r on rows [lo, RH - lo) and x on one more row.
-    // With few rows per thread the rows outside are skipped (a warp-uniform
-    // test, since a warp's rows share lj0); with PPT = 8 the per-row branches
-    // cost more instruction-level parallelism than the skipped rows save.
-    constexpr bool SKIP_ROWS = PPT <= 4;
+  // Rows whose values can still reach the interior after the remaining steps:
+  // step it must produce q, r on rows [lo, RH - lo) and x on one more row, with
+  // lo = T - (nsteps - 1 - it). With few rows per thread the rows outside are
+  // skipped (a warp-uniform test, since a warp's rows share lj0); with PPT = 8
+  // the per-row branches cost more instruction-level parallelism than the
+  // skipped rows save. (Running the tests only in the warps whose rows reach
+  // the top or bottom T rows of the region, with a test-free copy of the row
+  // loop for the others, raised the register count past the 64 that two
+  // blocks per SM allow.)
+  constexpr bool SKIP_ROWS = PPT <= 4;
+
+  // With two or four rows per thread the step loop is unrolled (nsteps <= T):
+  // the loop-carried registers need no copies between steps. With eight rows
+  // the unrolled steps need more than the 128 registers a thread may have
+  // (spills), and with one row (1024-thread blocks of small images) it was
+  // measured slower, so those keep the loop.
+  constexpr int STEP_UNROLL = (PPT == 2 || PPT == 4) ? T : 1;
+#pragma unroll STEP_UNROLL
+  for (int it = 0; it < T; ++it) {
+    if (it >= nsteps) break;
     const int lo = SKIP_ROWS ? T - (nsteps - 1 - it) : 0;
     const int hi = SKIP_ROWS ? RH - lo : RH;
     // phase 1: x = P_C(b - lam L^T r)
@@ -422,15 +438,107 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
   }
 }
 
-// Block-level choice between the fast interior path and the general one.
+// T iterations on a tile whose whole region lies outside the support of C, so
+// that x = P_C(.) = 0 on every pixel of the region: L x vanishes and each step
+// reduces to q = P_S(r), r' = q + beta (q - q_prev) pixel by pixel (the same
+// values the general body computes there). No neighbour is read, so the block
+// needs neither shared memory nor barriers, reads no b, and updates only the
+// interior pixels it owns.
+template <int TV, int T, int WX, int WY, int PPT, bool HIST>
+__device__ __forceinline__ void fgp_strip_zero(const Img& I, int j0, int k0, const float* beta, int nsteps,
+                                               bool first) {
+  constexpr int RW = 32 * WX, RH = PPT * WY;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int wx = warp % WX, wy = warp / WX;
+  const int lk = wx * 32 + lane;
+  const int lj0 = wy * PPT;
+  const int gk = k0 - T + lk;
+  const int gj0 = j0 - T + lj0;
+  if (lk < T || lk >= RW - T || (unsigned)gk >= (unsigned)I.n) return;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int lj = lj0 + s, gj = gj0 + s;
+    if (lj < T || lj >= RH - T || (unsigned)gj >= (unsigned)I.m) continue;
+    const long long o = (long long)gj * I.n + gk;
+    float4 q = z4, r = z4;
+    if (!first) {
+      q = __ldg(I.q_in + o);
+      r = __ldg(I.r_in + o);
+    }
+    for (int it = 0; it < nsteps; ++it) {
+      const float bt = beta[it];
+      const float4 qn = proj_S<TV>(r, I.alpha);
+      r = f4(qn.x + bt * (qn.x - q.x), qn.y + bt * (qn.y - q.y), qn.z + bt * (qn.z - q.z), qn.w + bt * (qn.w - q.w));
+      q = qn;
+      if (HIST) I.r_hist[it * I.hist_plane + o] = r;
+    }
+    if (!HIST || I.q_out != nullptr) {
+      I.q_out[o] = q;
+      I.r_out[o] = r;
+    }
+  }
+}
+
+// Block-level choice between the bodies: for a support rectangle, a region
+// entirely outside it takes the neighbour-free body and a region entirely inside
+// it (and inside the image) the amplitude-only (or unconstrained) fast path; a
+// region inside the image away from its last row and column takes the body
+// without edge tests.
 template <int TV, int T, int WX, int WY, int PPT, bool HIST, int CONS>
 __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, const float* beta, int nsteps,
                                                bool first) {
   constexpr int RW = 32 * WX, RH = PPT * WY;
   const int gj0 = j0 - T, gk0 = k0 - T;
   const bool inside = gj0 >= 0 && gk0 >= 0 && gj0 + RH <= I.m - 1 && gk0 + RW <= I.n - 1;
+  if constexpr (CONS == CONS_RECT) {
+    const ConsDev& c = I.C;
+    if (gj0 + RH <= c.j0 || gj0 >= c.j1 || gk0 + RW <= c.k0 || gk0 >= c.k1) {
+      fgp_strip_zero<TV, T, WX, WY, PPT, HIST>(I, j0, k0, beta, nsteps, first);
+      return;
+    }
+    if (inside && gj0 >= c.j0 && gj0 + RH <= c.j1 && gk0 >= c.k0 && gk0 + RW <= c.k1) {
+      if (c.amp) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_AMP>(I, j0, k0, beta, nsteps, first);
+      else fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_NONE>(I, j0, k0, beta, nsteps, first);
+      return;
+    }
+  }
   if (inside) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS>(I, j0, k0, beta, nsteps, first);
   else fgp_strip_body<TV, T, WX, WY, PPT, HIST, true, CONS>(I, j0, k0, beta, nsteps, first);
+}
+
+// FP32 sums that stay accurate without FP64 arithmetic (whose rate on this GPU
+// is a small fraction of FP32's). A running sum is a pair (s, c) updated by
+// Kahan's compensated addition: s - c is the sum to within an FP32 rounding of
+// the result, however many terms were added.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp-wide sum of a value held as an unevaluated pair hi + lo per lane, as a
+// pair again (hi the rounded sum, lo its error estimate); valid in lane 0.
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+    float s, e;
+    two_sum(hi, oh, s, e);
+    e += lo + ol;
+    hi = s + e;              // renormalise: hi + lo = s + e
+    lo = e - (hi - s);
+  }
 }
 
 // Block-wide FP64 sum of NV values; the result is valid in thread 0.

@@ -31,6 +31,26 @@ struct DenoiseCall {
   int plain_launches;   // nonzero: never build a stop graph (callers that must not allocate)
 };
 
+// Facts that hold for one device - a kernel's shared-memory limit, the SM count,
+// an occupancy, the tuned configurations - are kept per device ordinal, so that
+// one process can drive several GPUs. Ordinals at or above kMaxDevices are not
+// cached (every call then recomputes).
+constexpr int kMaxDevices = 64;
+inline int device_slot() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+  return d;
+}
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device.
+template <typename F>
+inline cudaError_t smem_attr_once(F* kernel, size_t bytes, bool (&done)[kMaxDevices]) {
+  const int d = device_slot();
+  if (d >= 0 && done[d]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && d >= 0) done[d] = true;
+  return e;
+}
+
 ctv_status run_denoise(const DenoiseCall& c);
 size_t denoise_workspace_bytes(int batch, int m, int n);
 bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out);

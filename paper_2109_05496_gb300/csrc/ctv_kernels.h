@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "ctv.h"
+#include "ctv_host.h"
 #include "ctv_device.cuh"
 #include "gap_device.cuh"
 
@@ -63,8 +64,11 @@ struct GapParams {
 };
 
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s);
-// Streaming multiprocessors of the current device (queried once).
+// Streaming multiprocessors of the current device (queried once per device).
 int sm_count();
+// Resident blocks per SM of `kernel` at `threads` threads on the current device
+// (queried once per device into `cached`).
+int occupancy_once(const void* kernel, int threads, int (&cached)[kMaxDevices]);
 // Per-TV-type launchers, instantiated one translation unit per type (pass_tv*.cu).
 template <int TV>
 cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);

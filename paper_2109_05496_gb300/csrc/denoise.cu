@@ -29,49 +29,145 @@
 
 namespace ctv {
 
-// Grid front end of gap_tile: blockIdx.z is the image of an equally sized batch.
-// (six resident blocks per SM: 40 registers, no spills; the tile loop is
-// latency-bound, so more blocks in flight hide more of each tile's loads)
-template <int TV>
-__global__ void __launch_bounds__(GAP_NT, 6) fgp_gap_kernel(GapParams p) {
-  __shared__ float4 qs[GAP_RW * GAP_RH];
-  __shared__ float2 xs[GAP_RW * GAP_RH];
-  __shared__ double red[3 * (GAP_NT / 32)];
+// Duality gap / finalize evaluation streamed down bands of rows by warps
+// (Eq. (18), problem (1), App. A Eq. (30)). A warp's 32 lanes cover 32 adjacent
+// columns and it owns the 30 of lanes 1..30: x at a lane needs q one column to
+// the left (lane - 1, by shuffle) and the TV summand needs x one column to the
+// right (lane + 1). It walks a band of GS_H rows top to bottom, one row per step,
+// keeping the previous row's p1 (the upper neighbour of L^T q) and x (the upper
+// end of the vertical difference) in registers, and loads GS_D rows ahead into a
+// register ring so that loads are in flight while it computes. No shared-memory
+// tiles and no block barriers until the final reduction: one pass over b and q
+// (24 B per pixel, 32/30 of the columns), plus x (8 B) for the final call.
+// The three sums are kept per lane in compensated FP32 (Kahan) over the band,
+// reduced across the warp as FP32 pairs without rounding loss and only then
+// turned into FP64 - once per warp: this GPU's FP64 rate is a small fraction of
+// its FP32 rate, and FP64 additions per group of rows had taken a third of the
+// kernel's time. One set of FP64 atomics per block commits the block's sums.
+constexpr int GS_WARPS = 8, GS_NT = 32 * GS_WARPS, GS_OWN = 30, GS_H = 32, GS_D = 4;
+
+template <int TV, int CONS>
+__global__ void __launch_bounds__(GS_NT, 3) fgp_gap_kernel(GapParams p) {
+  __shared__ double wsum[3][GS_WARPS];
   __shared__ int last;
   const int z = blockIdx.z;
   DevStats* st = p.st + z;
   const int stopped = *(volatile int*)&st->stop;
   if (!p.final_call && stopped) return;
   const int set = stopped ? st->stop_set : p.default_set;
-  GapImg g;
-  g.b = p.b + z * p.b_stride;
-  g.ld = p.ld;
+  const int m = p.m, n = p.n;
+  const float2* b = p.b + z * p.b_stride;
   const bool zq = p.zero_q != 0 && !stopped;
-  const float4* q = set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in);
-  g.q = zq ? nullptr : q + z * p.d_stride;
-  g.x = p.x != nullptr ? p.x + z * p.x_stride : nullptr;
-  g.q_export = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
-  g.m = p.m;
-  g.n = p.n;
-  float lam = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
-  const bool bad_lam = !(lam >= 0.f);
-  g.lam = bad_lam ? 0.f : lam;
-  g.alpha = p.alpha;
-  g.C = p.C;
-  // blocks loop over the image's tiles (few blocks, so that a launch after the
-  // stop costs little and the FP64 atomics stay few)
-  double acc[3] = {0.0, 0.0, 0.0};
+  const float4* q = zq ? nullptr : (set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in)) + z * p.d_stride;
+  float2* x_out = p.x != nullptr ? p.x + z * p.x_stride : nullptr;
+  float4* q_exp = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
+  const float lv = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
+  const bool bad_lam = !(lv >= 0.f);
+  const float lam = bad_lam ? 0.f : lv;
+  const float alpha = p.alpha;
+  const ConsDev C = p.C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncw = (n + GS_OWN - 1) / GS_OWN, nbr = (m + GS_H - 1) / GS_H;
+  const int g = blockIdx.x * GS_WARPS + warp;
+  float ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};   // compensated per-lane sums
   bool nf = false;
-  const int tx = (p.n + GAP_RW - 3) / (GAP_RW - 2), ty = (p.m + GAP_RH - 3) / (GAP_RH - 2);
-  for (int t = blockIdx.x; t < tx * ty; t += gridDim.x) {
-    const int by = t / tx, bx = t - by * tx;
-    gap_tile_add<TV>(g, by * (GAP_RH - 2), bx * (GAP_RW - 2), qs, xs, acc, nf);
-    __syncthreads();
+  if (g < ncw * nbr) {   // warp-uniform
+    const int bc = g % ncw, br = g / ncw;
+    const int k = bc * GS_OWN - 1 + lane;
+    const bool kin = (unsigned)k < (unsigned)n;
+    const bool own = lane >= 1 && lane <= GS_OWN && kin;
+    const bool has_right = k < n - 1;
+    const bool kin_rect = k >= C.k0 && k < C.k1;   // column inside a support rectangle
+    const int jA = br * GS_H, jB = min(jA + GS_H, m);
+    const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+    float4 rq[GS_D];
+    float2 rb[GS_D];
+    auto load = [&](int j, float4& qv, float2& bv) {
+      qv = z4;
+      bv = make_float2(0.f, 0.f);
+      if (kin && (unsigned)j < (unsigned)m) {
+        if (q != nullptr) qv = __ldg(q + (long long)j * n + k);
+        bv = __ldg(b + (long long)j * p.ld + k);
+      }
+    };
+#pragma unroll
+    for (int u = 0; u < GS_D; ++u) load(jA - 1 + u, rq[u], rb[u]);
+    float2 p1u = make_float2(0.f, 0.f);   // p1 of the row above
+    float2 xu = make_float2(0.f, 0.f);    // x of the row above
+    // rows jA - 1 (its p1 only) to jB (its x only, for the vertical difference of row jB - 1);
+    // the ring slot of a row is a compile-time index (the rows are walked in groups of
+    // GS_D, the last group guarded rather than cut short)
+    for (int j0 = jA - 1; j0 <= jB; j0 += GS_D) {
+#pragma unroll
+      for (int u = 0; u < GS_D; ++u) {
+        const int j = j0 + u;
+        if (j <= jB) {   // warp-uniform, like every row test below
+          const float4 qc = rq[u];
+          const float2 bb = rb[u];
+          if (j + GS_D <= jB) load(j + GS_D, rq[u], rb[u]);
+          // p2 of the left neighbour from lane - 1 (lane 0's x is never used)
+          const float l2r = __shfl_up_sync(0xffffffffu, qc.z, 1);
+          const float l2i = __shfl_up_sync(0xffffffffu, qc.w, 1);
+          // x of the right neighbour in the row above, from lane + 1
+          const float xrr = __shfl_down_sync(0xffffffffu, xu.x, 1);
+          const float xri = __shfl_down_sync(0xffffffffu, xu.y, 1);
+          const bool row_in = j >= jA && j < m;
+          float2 xc = make_float2(0.f, 0.f);
+          float dlr = 0.f, dli = 0.f, wr = 0.f, wi = 0.f;
+          if (row_in) {
+            // (L^T q)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]; x = P_C(b - lam L^T q)
+            // with one fused multiply-add per part, as in every kernel that evaluates
+            // Eq. (18) at the end of a solve, so that all of them give the same bits
+            const float tr = qc.x - p1u.x + qc.z - l2r, ti = qc.y - p1u.y + qc.w - l2i;
+            xc = proj_C_t<CONS>(make_float2(fmaf(-lam, tr, bb.x), fmaf(-lam, ti, bb.y)), j, k, kin_rect, C);
+            dlr = lam * tr;
+            dli = lam * ti;
+            wr = bb.x - dlr;
+            wi = bb.y - dli;
+          }
+          if (own && j > jA) {
+            // TV summand of row j - 1: d1 = x[j-1,k] - x[j,k] (none on the last row),
+            // d2 = x[j-1,k] - x[j-1,k+1] (none on the last column)
+            const float d1r = j < m ? xu.x - xc.x : 0.f, d1i = j < m ? xu.y - xc.y : 0.f;
+            const float d2r = has_right ? xu.x - xrr : 0.f, d2i = has_right ? xu.y - xri : 0.f;
+            kahan_add(ks[1], kc[1], tv_term<TV>(d1r, d1i, d2r, d2i, alpha));
+          }
+          if (own && row_in && j < jB) {
+            nf |= nonfinite2(bb);
+            const float er = xc.x - bb.x, ei = xc.y - bb.y;
+            kahan_add(ks[0], kc[0], er * er + ei * ei);
+            // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
+            const float hr = wr - xc.x, hi = wi - xc.y;
+            kahan_add(ks[2], kc[2], (2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (hr * hr + hi * hi));
+            if (x_out != nullptr) x_out[(long long)j * p.ld + k] = xc;
+            if (q_exp != nullptr) q_exp[(long long)j * n + k] = qc;
+          }
+          xu = xc;
+          p1u = make_float2(qc.x, qc.y);
+        }
+      }
+    }
+  }
+  // the lane's sum is ks - kc; warp sums as FP32 pairs, then FP64 per warp
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float hi = ks[a], lo = -kc[a];
+    warp_sum_pair(hi, lo);
+    if (lane == 0) wsum[a][warp] = (double)hi + (double)lo;
   }
   const bool block_nf = __syncthreads_or(nf) != 0;
   if (block_nf && threadIdx.x == 0) raise_async(CTV_ENONFINITE);
-  block_sum<GAP_NT, 3>(acc, red);
-  gap_commit(st, acc, gridDim.x, 1u, g.lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last, block_nf);
+  // (__syncthreads_or above also ordered the warps' wsum stores)
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < GS_WARPS; ++w) {
+      acc[0] += wsum[0][w];
+      acc[1] += wsum[1][w];
+      acc[2] += wsum[2][w];
+    }
+  }
+  gap_commit(st, acc, gridDim.x, 1u, lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last, block_nf);
   // inside a stop graph, the check that stops the solve skips the remaining intervals
   if (p.n_cond > 0 && threadIdx.x == 0 && last && st->stop)
     for (int i = 0; i < p.n_cond; ++i) cudaGraphSetConditional(p.cond[i], 0u);
@@ -132,7 +228,7 @@ __global__ void __launch_bounds__(FIN_NT) fgp_finalize_kernel(GapParams p) {
     const float2 bb = __ldg(b + (long long)j * p.ld + k);
     nf |= nonfinite2(bb);
     x[(long long)j * p.ld + k] =
-        proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)), j, k,
+        proj_C(make_float2(fmaf(-lam, qc.x - qu.x + qc.z - ql.z, bb.x), fmaf(-lam, qc.y - qu.y + qc.w - ql.w, bb.y)), j, k,
                p.C);
     if (qe != nullptr) qe[o] = qc;
   }
@@ -156,44 +252,50 @@ cudaError_t launch_finalize(const GapParams& p, int batch, cudaStream_t s) {
 int take_async_status_denoise() { return take_unit_async_status(); }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 0;
-    if (n <= 0) n = 1;
-  }
+  static int cached[kMaxDevices] = {};
+  const int d = device_slot();
+  if (d >= 0 && cached[d] > 0) return cached[d];
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n = 0;
+  if (n <= 0) n = 1;
+  if (d >= 0) cached[d] = n;
   return n;
 }
 
+// Resident blocks per SM of a kernel at `threads` threads (and no dynamic shared
+// memory), once per device and kernel.
+int occupancy_once(const void* kernel, int threads, int (&cached)[kMaxDevices]) {
+  const int d = device_slot();
+  if (d >= 0 && cached[d] > 0) return cached[d];
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0)
+    per_sm = 1;
+  if (d >= 0) cached[d] = per_sm;
+  return per_sm;
+}
+
 template <int TV>
-static int gap_blocks(const GapParams& p) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_gap_kernel<TV>, GAP_NT, 0) != cudaSuccess ||
-        per_sm <= 0)
-      per_sm = 1;
+static void launch_gap_tv(const GapParams& p, dim3 grid, cudaStream_t s) {
+  switch (cons_mode(p.C)) {
+    case CONS_NONE: fgp_gap_kernel<TV, CONS_NONE><<<grid, GS_NT, 0, s>>>(p); break;
+    case CONS_AMP: fgp_gap_kernel<TV, CONS_AMP><<<grid, GS_NT, 0, s>>>(p); break;
+    case CONS_RECT: fgp_gap_kernel<TV, CONS_RECT><<<grid, GS_NT, 0, s>>>(p); break;
+    default: fgp_gap_kernel<TV, CONS_GEN><<<grid, GS_NT, 0, s>>>(p); break;
   }
-  const long long tiles = (long long)((p.n + GAP_RW - 3) / (GAP_RW - 2)) * ((p.m + GAP_RH - 3) / (GAP_RH - 2));
-  const long long cap = (long long)per_sm * sm_count();
-  return (int)(tiles < cap ? tiles : cap);
 }
 
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
-  int nb = 1;
+  // one warp per band of GS_H rows and GS_OWN columns
+  const long long warps = (long long)((p.n + GS_OWN - 1) / GS_OWN) * ((p.m + GS_H - 1) / GS_H);
+  const long long blocks = (warps + GS_WARPS - 1) / GS_WARPS;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)blocks, 1, batch);
   switch (tv) {
-    case TV1_ISO: nb = gap_blocks<TV1_ISO>(p); break;
-    case TV1_ANISO: nb = gap_blocks<TV1_ANISO>(p); break;
-    case TV2_ISO: nb = gap_blocks<TV2_ISO>(p); break;
-    case TV2_ANISO: nb = gap_blocks<TV2_ANISO>(p); break;
-    default: return cudaErrorInvalidValue;
-  }
-  dim3 grid(nb, 1, batch);
-  switch (tv) {
-    case TV1_ISO: fgp_gap_kernel<TV1_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
-    case TV1_ANISO: fgp_gap_kernel<TV1_ANISO><<<grid, GAP_NT, 0, s>>>(p); break;
-    case TV2_ISO: fgp_gap_kernel<TV2_ISO><<<grid, GAP_NT, 0, s>>>(p); break;
-    case TV2_ANISO: fgp_gap_kernel<TV2_ANISO><<<grid, GAP_NT, 0, s>>>(p); break;
+    case TV1_ISO: launch_gap_tv<TV1_ISO>(p, grid, s); break;
+    case TV1_ANISO: launch_gap_tv<TV1_ANISO>(p, grid, s); break;
+    case TV2_ISO: launch_gap_tv<TV2_ISO>(p, grid, s); break;
+    case TV2_ANISO: launch_gap_tv<TV2_ANISO>(p, grid, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

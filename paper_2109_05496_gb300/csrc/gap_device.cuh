@@ -3,7 +3,6 @@
 // reduced in FP64.
 #pragma once
 
-#include "async_status.cuh"
 #include "ctv_device.cuh"
 
 namespace ctv {
@@ -69,7 +68,7 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
       const float4 qu = lj > 0 ? qs[i - RW] : z4;
       const float4 ql = lk > 0 ? qs[i - 1] : z4;
       const float2 bb = bv[s];
-      xv = proj_C(make_float2(bb.x - lam * (qc.x - qu.x + qc.z - ql.z), bb.y - lam * (qc.y - qu.y + qc.w - ql.w)),
+      xv = proj_C(make_float2(fmaf(-lam, qc.x - qu.x + qc.z - ql.z, bb.x), fmaf(-lam, qc.y - qu.y + qc.w - ql.w, bb.y)),
                   gj, gk, g.C);
     }
     xs[i] = xv;

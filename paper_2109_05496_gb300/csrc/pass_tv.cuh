@@ -8,6 +8,7 @@
 
 #include "ctv_configs.cuh"
 #include "ctv_device.cuh"
+#include "ctv_host.h"
 #include "ctv_kernels.h"
 
 namespace ctv {
@@ -17,7 +18,8 @@ namespace ctv {
 #endif
 
 template <int KIND, int TV, int T, int A, int B, int C, int CONS>
-__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(PassParams p) {
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B, C>::MINB)
+    fgp_pass_kernel(PassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
 #if CTV_PDL
   // Programmatic dependent launch: the next pass may be scheduled onto SMs this
@@ -51,13 +53,9 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_kernel(Pa
 template <int KIND, int TV, int T, int A, int B, int C, int CONS>
 static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
   using G = CfgGeom<KIND, A, B, C>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static bool attr_done[kMaxDevices] = {};
+  cudaError_t e = smem_attr_once(fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>, G::SMEM, attr_done);
+  if (e != cudaSuccess) return e;
 #if CTV_PDL
   cudaLaunchConfig_t lc;
   memset(&lc, 0, sizeof(lc));

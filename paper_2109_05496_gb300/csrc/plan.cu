@@ -59,7 +59,8 @@ struct ListPassParams {
 };
 
 template <int KIND, int TV, int CONS, int T, int A, int B, int C>
-__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kernel(ListPassParams p) {
+__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B, C>::MINB)
+    fgp_pass_list_kernel(ListPassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
   const WorkItem w = p.items[blockIdx.x];
   // fields read from global memory one by one (a register copy of the
@@ -83,13 +84,14 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_pass_list_kern
   const int j0 = (w.tile / d.tiles_x) * (G::RH - 2 * T), k0 = (w.tile % d.tiles_x) * (G::RW - 2 * T);
   // The extrapolation weights go through shared memory: indexing the parameter
   // array by the runtime step number would copy the whole parameter block into
-  // local memory. The tile's first barrier (after its loads) orders these
-  // stores before the first use.
+  // local memory. (Some tile bodies have no barrier of their own, so one orders
+  // these stores before the first use.)
   __shared__ float beta_s[8];
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) beta_s[i] = p.beta[i];
   }
+  __syncthreads();
   run_tile<KIND, TV, T, A, B, C, false, CONS>(I, j0, k0, beta_s, p.nsteps, p.first != 0);
 }
 
@@ -177,12 +179,8 @@ int take_async_status_plan() { return take_unit_async_status(); }
 
 // Blocks of a gap / finalize launch: resident blocks, at most one per item.
 static int gap_list_blocks(int n_items) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_gap_list_kernel, GAP_NT, 0) != cudaSuccess ||
-        per_sm <= 0)
-      per_sm = 1;
-  }
+  static int per_sm_cache[kMaxDevices] = {};
+  const int per_sm = occupancy_once((const void*)fgp_gap_list_kernel, GAP_NT, per_sm_cache);
   const long long cap = (long long)per_sm * sm_count();
   return (int)(n_items < cap ? n_items : cap);
 }
