@@ -326,7 +326,7 @@ def main():
     peak, peak_kind = read_peaks()
     per_launch_units = units.value / max(pass_n.value, 1)
     achieved = ALGO_BYTES_PER_PX_IT * units.value / (pass_ms.value * 1e-3) / 1e9 if pass_ms.value > 0 else None
-    cfg_used = args.config if args.config >= 0 else default_config_id(lib)
+    cfg_used = args.config if args.config >= 0 else default_config_id(lib, rect)
     traffic = profiled_traffic(config_geometry(lib, cfg_used), per_launch_units)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -401,12 +401,18 @@ def main():
         dist.destroy_process_group()
 
 
-def default_config_id(lib) -> int:
-    return int(lib.ctv_default_config(M, N, ITERS, 0))
+def default_config_id(lib, rect) -> int:
+    import ctypes
+    from paper_2109_05496_gb300 import api
+    cc, _ = api.Constraint(amp_max=1.0, rect=rect).to_c()
+    return int(lib.ctv_default_config(M, N, ITERS, 0, ctypes.byref(cc)))
 
 
 def default_config_small(lib) -> int:
-    return int(lib.ctv_default_config(256, 256, 100, 0))
+    import ctypes
+    from paper_2109_05496_gb300 import api
+    cc, _ = api.Constraint(amp_max=1.0).to_c()
+    return int(lib.ctv_default_config(256, 256, 100, 0, ctypes.byref(cc)))
 
 
 # ----------------------------------------------------------------------------- other workloads

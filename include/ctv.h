@@ -145,8 +145,9 @@ int ctv_get_last_error(ctv_stream stream);
 int ctv_num_configs(void);
 int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads);
 /* The configuration that opts->config = -1 selects for an m x n image, K
- * iterations and a TV type (the autotuned choice when there is one). */
-int ctv_default_config(int m, int n, int iters, int tv_type);
+ * iterations, a TV type and the set C (NULL: no constraint) - the autotuned
+ * choice when there is one. -1 if C is invalid. */
+int ctv_default_config(int m, int n, int iters, int tv_type, const ctv_constraint* C);
 
 /* Autotuner (no counterpart in the paper). ctv_autotune_denoise runs
  * ctv_denoise once per configuration plus `repeats` timed times on the caller's

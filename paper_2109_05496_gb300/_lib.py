@@ -53,7 +53,7 @@ SIGNATURES = {
     "ctv_abi_version": (c_int, []),
     "ctv_get_last_error": (c_int, [c_void_p]),
     "ctv_num_configs": (c_int, []),
-    "ctv_default_config": (c_int, [c_int, c_int, c_int, c_int]),
+    "ctv_default_config": (c_int, [c_int, c_int, c_int, c_int, P(CtvConstraint)]),
     "ctv_config_info": (c_int, [c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
     "ctv_denoise_workspace_size": (c_size_t, [c_int, c_int, c_int]),
     "ctv_size_class": (c_int, [c_int, c_int]),

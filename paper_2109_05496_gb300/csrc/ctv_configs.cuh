@@ -47,13 +47,23 @@ struct CfgGeom {
                               : (C <= 4 && NT <= 512) ? 65536 / (NT * 64) : 1;
 };
 
-template <int KIND, int TV, int T, int A, int B, int C, bool HIST = false, int CONS = CONS_GEN>
-__device__ __forceinline__ void run_tile(const Img& I, int j0, int k0, const float* beta, int nsteps, bool first) {
+template <int KIND, int TV, int T, int A, int B, int C, bool HIST = false, int CONS = CONS_GEN, bool GAPEV = false>
+__device__ __forceinline__ void run_tile(const Img& I, int j0, int k0, const float* beta, int nsteps, bool first,
+                                         GapSums* gs = nullptr) {
   if constexpr (KIND == 0) {
+    static_assert(!GAPEV, "region tiles do not evaluate the gap");
     fgp_tile<TV, T, A, B, C, HIST>(I, j0, k0, beta, nsteps, first);
   } else {
-    fgp_strip_tile<TV, T, A, B, C, HIST, CONS>(I, j0, k0, beta, nsteps, first);
+    fgp_strip_tile<TV, T, A, B, C, HIST, CONS, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
   }
 }
+
+// Configurations whose pass can end a check interval with the duality-gap
+// evaluation fused in (column strips of at most four rows per thread, within
+// their register budget).
+template <int KIND, int C>
+struct GapEvalOk {
+  static constexpr bool value = KIND == 1 && C <= 4;
+};
 
 }  // namespace ctv

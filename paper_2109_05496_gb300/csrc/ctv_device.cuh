@@ -46,6 +46,83 @@ __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { retur
 // Non-finite test of one complex input value (NaN or an infinity in either part).
 __device__ __forceinline__ bool nonfinite2(float2 v) { return !(isfinite(v.x) && isfinite(v.y)); }
 
+// FP32 sums that stay accurate without FP64 arithmetic (whose rate on this GPU
+// is a small fraction of FP32's). A running sum is a pair (s, c) updated by
+// Kahan's compensated addition: s - c is the sum to within an FP32 rounding of
+// the result, however many terms were added.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp-wide sum of a value held as an unevaluated pair hi + lo per lane, as a
+// pair again (hi the rounded sum, lo its error estimate); valid in lane 0.
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+    float s, e;
+    two_sum(hi, oh, s, e);
+    e += lo + ol;
+    hi = s + e;              // renormalise: hi + lo = s + e
+    lo = e - (hi - s);
+  }
+}
+
+
+// (hi, lo) += (h2, l2) for unevaluated FP32 pairs, without rounding loss beyond
+// FP32^2 relative.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
+  float s, e;
+  two_sum(hi, h2, s, e);
+  e += lo + l2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Block-wide sum of NV values held as FP32 pairs (hi, lo) per thread; the result
+// is valid in thread 0. red: shared memory of NV * NT / 32 float2.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum_pairs(float (&hi)[NV], float (&lo)[NV], float2* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    warp_sum_pair(hi[a], lo[a]);
+    if (lane == 0) red[a * (NT / 32) + warp] = make_float2(hi[a], lo[a]);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const float2 v = lane < NT / 32 ? red[a * (NT / 32) + lane] : make_float2(0.f, 0.f);
+      hi[a] = v.x;
+      lo[a] = v.y;
+      warp_sum_pair(hi[a], lo[a]);
+    }
+  }
+}
+
+// One thread's share of the duality-gap terms of problem (1) at a dual point q
+// (App. A): ||x - b||^2, TV(x) and ||b||^2 - ||w||^2 + ||w - P_C(w)||^2 with
+// w = b - lam L^T q and x = P_C(w), as FP32 sums s (minus the compensation c of
+// the bodies that add many terms per thread), and whether a value of b was a
+// NaN or an infinity.
+struct GapSums {
+  float s[3], c[3];
+  bool nf;
+};
+
+
 // P_C: support first (x = 0 outside), then the amplitude bound of Eq. (26),
 // x * amax / max{amax, |x|}, or the box on the real and imaginary parts.
 __device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev& c) {
@@ -293,9 +370,11 @@ __device__ __forceinline__ float2 proj_C_t(float2 w, int gj, int gk, bool kin, c
 // neighbour of the next strip) - and b.
 // EDGE = false is the fast path for regions that lie inside the image away
 // from its last row and column: no per-pixel bounds or edge tests.
-template <int TV, int T, int WX, int WY, int PPT, bool HIST, bool EDGE, int CONS>
+// GAPEV: the pass ends a check interval (nsteps <= T - 1) and also adds the
+// block's share of the duality-gap terms at the final q into gs (see below).
+template <int TV, int T, int WX, int WY, int PPT, bool HIST, bool EDGE, int CONS, bool GAPEV = false>
 __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, const float* beta, int nsteps,
-                                               bool first) {
+                                               bool first, GapSums* gs = nullptr) {
   constexpr int RW = 32 * WX, RH = PPT * WY, R = RW * RH;
   extern __shared__ float4 smem4[];
   float2* P2 = reinterpret_cast<float2*>(smem4);      // R
@@ -367,7 +446,8 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
 #pragma unroll STEP_UNROLL
   for (int it = 0; it < T; ++it) {
     if (it >= nsteps) break;
-    const int lo = SKIP_ROWS ? T - (nsteps - 1 - it) : 0;
+    // (a pass that evaluates the gap afterwards keeps one more ring of rows exact)
+    const int lo = SKIP_ROWS ? T - (GAPEV ? 1 : 0) - (nsteps - 1 - it) : 0;
     const int hi = SKIP_ROWS ? RH - lo : RH;
     // phase 1: x = P_C(b - lam L^T r)
 #pragma unroll
@@ -436,6 +516,59 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
       }
     }
   }
+
+  if constexpr (GAPEV) {
+    // The duality-gap terms at q_k (the final q of this pass) on the interior,
+    // from the state the block holds. After nsteps <= T - 1 steps q_k is exact on
+    // the interior and one ring around it, which is all that x = P_C(b - lam L^T
+    // q_k) (Eq. (18)) on the interior and on its lower and right neighbours needs.
+    // The last step ended with a barrier, so p2 and p1 of q_k may replace r's.
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) P2[(lj0 + s) * RW + lk] = make_float2(q[s].z, q[s].w);
+    P1B[wy * RW + lk] = make_float2(q[PPT - 1].x, q[PPT - 1].y);
+    __syncthreads();
+    const bool colint = lk >= T && lk < RW - T && colin;
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int lj = lj0 + s, gj = gj0 + s;
+      // the terms read x on the interior rows and the row below them
+      if (SKIP_ROWS && (lj < T || lj > RH - T)) continue;
+      x[s] = z2;
+      if (!TESTS || (colin && (unsigned)gj < (unsigned)I.m)) {
+        float2 up;
+        if (s > 0) up = make_float2(q[s - 1].x, q[s - 1].y);
+        else up = wy > 0 ? P1B[(wy - 1) * RW + lk] : z2;
+        const float2 left = lk > 0 ? P2[(lj0 + s) * RW + lk - 1] : z2;
+        const float tr = q[s].x - up.x + q[s].z - left.x, ti = q[s].y - up.y + q[s].w - left.y;
+        const float2 bb = Bs[(lj0 + s) * RW + lk];
+        x[s] = proj_C_t<CONS>(make_float2(fmaf(-lam, tr, bb.x), fmaf(-lam, ti, bb.y)), gj, gk, kin, I.C);
+        if (colint && lj >= T && lj < RH - T && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
+          gs->nf |= nonfinite2(bb);
+          const float er = x[s].x - bb.x, ei = x[s].y - bb.y;
+          gs->s[0] += er * er + ei * ei;
+          // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
+          const float dlr = lam * tr, dli = lam * ti;
+          const float hr = (bb.x - dlr) - x[s].x, hi = (bb.y - dli) - x[s].y;
+          gs->s[2] += (2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (hr * hr + hi * hi);
+        }
+      }
+      X[(lj0 + s) * RW + lk] = x[s];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      const int lj = lj0 + s, gj = gj0 + s;
+      if (colint && lj >= T && lj < RH - T && (!EDGE || (unsigned)gj < (unsigned)I.m)) {
+        // interior rows end T rows above the region's last row, so the lower
+        // neighbour is in the region
+        const float2 xd = s < PPT - 1 ? x[s + 1] : X[(lj0 + s + 1) * RW + lk];
+        const float2 xr = X[(lj0 + s) * RW + lk + 1];
+        const bool d1 = !EDGE || gj < I.m - 1, d2 = !EDGE || gk < I.n - 1;
+        gs->s[1] += tv_term<TV>(d1 ? x[s].x - xd.x : 0.f, d1 ? x[s].y - xd.y : 0.f, d2 ? x[s].x - xr.x : 0.f,
+                                d2 ? x[s].y - xr.y : 0.f, I.alpha);
+      }
+    }
+  }
 }
 
 // T iterations on a tile whose whole region lies outside the support of C, so
@@ -444,9 +577,9 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
 // values the general body computes there). No neighbour is read, so the block
 // needs neither shared memory nor barriers, reads no b, and updates only the
 // interior pixels it owns.
-template <int TV, int T, int WX, int WY, int PPT, bool HIST>
+template <int TV, int T, int WX, int WY, int PPT, bool HIST, bool GAPEV = false>
 __device__ __forceinline__ void fgp_strip_zero(const Img& I, int j0, int k0, const float* beta, int nsteps,
-                                               bool first) {
+                                               bool first, GapSums* gs = nullptr) {
   constexpr int RW = 32 * WX, RH = PPT * WY;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -478,6 +611,15 @@ __device__ __forceinline__ void fgp_strip_zero(const Img& I, int j0, int k0, con
       I.q_out[o] = q;
       I.r_out[o] = r;
     }
+    if constexpr (GAPEV) {
+      // x = 0 here and at every neighbour: TV(x) adds nothing, ||x - b||^2 = ||b||^2,
+      // and w - P_C(w) = w turns the dual part into ||b||^2 as well
+      const float2 bb = __ldg(I.b + (long long)gj * I.ld + gk);
+      gs->nf |= nonfinite2(bb);
+      const float b2 = bb.x * bb.x + bb.y * bb.y;
+      gs->s[0] += b2;
+      gs->s[2] += b2;
+    }
   }
 }
 
@@ -486,59 +628,26 @@ __device__ __forceinline__ void fgp_strip_zero(const Img& I, int j0, int k0, con
 // it (and inside the image) the amplitude-only (or unconstrained) fast path; a
 // region inside the image away from its last row and column takes the body
 // without edge tests.
-template <int TV, int T, int WX, int WY, int PPT, bool HIST, int CONS>
+template <int TV, int T, int WX, int WY, int PPT, bool HIST, int CONS, bool GAPEV = false>
 __device__ __forceinline__ void fgp_strip_tile(const Img& I, int j0, int k0, const float* beta, int nsteps,
-                                               bool first) {
+                                               bool first, GapSums* gs = nullptr) {
   constexpr int RW = 32 * WX, RH = PPT * WY;
   const int gj0 = j0 - T, gk0 = k0 - T;
   const bool inside = gj0 >= 0 && gk0 >= 0 && gj0 + RH <= I.m - 1 && gk0 + RW <= I.n - 1;
   if constexpr (CONS == CONS_RECT) {
     const ConsDev& c = I.C;
     if (gj0 + RH <= c.j0 || gj0 >= c.j1 || gk0 + RW <= c.k0 || gk0 >= c.k1) {
-      fgp_strip_zero<TV, T, WX, WY, PPT, HIST>(I, j0, k0, beta, nsteps, first);
+      fgp_strip_zero<TV, T, WX, WY, PPT, HIST, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
       return;
     }
     if (inside && gj0 >= c.j0 && gj0 + RH <= c.j1 && gk0 >= c.k0 && gk0 + RW <= c.k1) {
-      if (c.amp) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_AMP>(I, j0, k0, beta, nsteps, first);
-      else fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_NONE>(I, j0, k0, beta, nsteps, first);
+      if (c.amp) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_AMP, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
+      else fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS_NONE, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
       return;
     }
   }
-  if (inside) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS>(I, j0, k0, beta, nsteps, first);
-  else fgp_strip_body<TV, T, WX, WY, PPT, HIST, true, CONS>(I, j0, k0, beta, nsteps, first);
-}
-
-// FP32 sums that stay accurate without FP64 arithmetic (whose rate on this GPU
-// is a small fraction of FP32's). A running sum is a pair (s, c) updated by
-// Kahan's compensated addition: s - c is the sum to within an FP32 rounding of
-// the result, however many terms were added.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// Warp-wide sum of a value held as an unevaluated pair hi + lo per lane, as a
-// pair again (hi the rounded sum, lo its error estimate); valid in lane 0.
-__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-    float s, e;
-    two_sum(hi, oh, s, e);
-    e += lo + ol;
-    hi = s + e;              // renormalise: hi + lo = s + e
-    lo = e - (hi - s);
-  }
+  if (inside) fgp_strip_body<TV, T, WX, WY, PPT, HIST, false, CONS, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
+  else fgp_strip_body<TV, T, WX, WY, PPT, HIST, true, CONS, GAPEV>(I, j0, k0, beta, nsteps, first, gs);
 }
 
 // Block-wide FP64 sum of NV values; the result is valid in thread 0.

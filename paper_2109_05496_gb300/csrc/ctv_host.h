@@ -53,9 +53,23 @@ inline cudaError_t smem_attr_once(F* kernel, size_t bytes, bool (&done)[kMaxDevi
 
 ctv_status run_denoise(const DenoiseCall& c);
 size_t denoise_workspace_bytes(int batch, int m, int n);
+
+// Workspace of a solve: per image a statistics record (DevStats, at most 256 B)
+// and a slot array of block partial sums of the duality-gap reduction (4
+// doubles per block, as many blocks as a launch over the image can have: one per
+// 16 x 16 pixels or more), then two dual buffer sets (q, r) of float4 per pixel.
+constexpr size_t ws_align256(size_t v) { return (v + 255) & ~(size_t)255; }
+constexpr size_t gap_slots_per_image(int m, int n) { return (size_t)((m + 15) / 16) * (size_t)((n + 15) / 16); }
+constexpr size_t denoise_workspace_bytes_c(int batch, int m, int n) {
+  return (batch <= 0 || m <= 0 || n <= 0)
+             ? 0
+             : ws_align256((size_t)batch * 256) + ws_align256((size_t)batch * gap_slots_per_image(m, n) * 32) +
+                   4 * ws_align256((size_t)batch * (size_t)m * (size_t)n * 16);
+}
 bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out);
 void nesterov_betas(int K, std::vector<double>* beta);
-int default_config(int m, int n, int iters, int tv);
+// cons: the constraint specialisation (CONS_*) of the solve's C
+int default_config(int m, int n, int iters, int tv, int cons);
 int tuned_config(int m, int n, int tv);   // -1 when the size class / TV type is not tuned
 int size_class(int m, int n);
 int num_configs();

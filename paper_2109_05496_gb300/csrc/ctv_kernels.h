@@ -10,6 +10,9 @@
 
 namespace ctv {
 
+// Check intervals a stop graph can hold (solves with more run as plain launches).
+#define CTV_MAX_STOP_INTERVALS 64
+
 // One launch of the fused FGP pass over an equally sized batch (blockIdx.z = image).
 struct PassParams {
   const float2* b;
@@ -29,10 +32,14 @@ struct PassParams {
   float beta[8];
   int nsteps;
   int first;
+  // a pass that ends a check interval with the duality-gap terms evaluated in it
+  // (gap_eval != 0, strip configurations only): each block stores its sums in its
+  // slot of the image's slot array and fgp_gap_finish_kernel evaluates them
+  int gap_eval;
+  DevStats* gst;
+  float* slots;
+  long long slot_stride;
 };
-
-// Check intervals a stop graph can hold (solves with more run as plain launches).
-#define CTV_MAX_STOP_INTERVALS 64
 
 // One launch of the finalize / gap evaluation over an equally sized batch.
 struct GapParams {
@@ -54,6 +61,8 @@ struct GapParams {
   float alpha;
   ConsDev C;
   DevStats* st;
+  float* slots;           // block partial sums of the reduction (slot_stride floats per image)
+  long long slot_stride;
   int iter;
   double gap_tol;
   int final_call;
@@ -72,6 +81,11 @@ int occupancy_once(const void* kernel, int threads, int (&cached)[kMaxDevices]);
 // Per-TV-type launchers, instantiated one translation unit per type (pass_tv*.cu).
 template <int TV>
 cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);
+// The same with the duality gap evaluated in the pass (pass_gap_tv*.cu); only for
+// configurations with pass_gap_eval_ok(cfg).
+template <int TV>
+cudaError_t launch_pass_gap_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s);
+bool pass_gap_eval_ok(int cfg);
 // Constraint specialisation (CONS_*) of a constraint descriptor.
 inline int cons_mode(const ConsDev& c) {
   if (c.box) return CONS_GEN;
@@ -79,6 +93,26 @@ inline int cons_mode(const ConsDev& c) {
   if (c.sup == 1) return CONS_RECT;
   return CONS_GEN;
 }
+// Evaluation of a reduction stored in per-block slots (gap_store_slot): one block
+// per image adds the nblk slots and turns them into primal, dual and gap, applies
+// the stopping test of a check or records the final statistics, and inside a stop
+// graph clears the later intervals' handles when the test passes.
+struct GapFinishParams {
+  DevStats* st;
+  const float* slots;
+  long long slot_stride;
+  unsigned nblk;
+  float lam;
+  const float* lam_dev;
+  int set;   // the dual set holding q at this check (recorded at a stop)
+  int iter;
+  double gap_tol;
+  int final_call;
+  int n_cond;
+  cudaGraphConditionalHandle cond[CTV_MAX_STOP_INTERVALS];
+};
+cudaError_t launch_gap_finish(const GapFinishParams& f, int batch, cudaStream_t s);
+// The gap / finalize evaluation (two kernels: the evaluation and its finish).
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s);
 // x = P_C(b - lam L^T q) only (no objective terms, no statistics record)
 cudaError_t launch_finalize(const GapParams& p, int batch, cudaStream_t s);

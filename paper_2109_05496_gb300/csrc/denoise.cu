@@ -1,13 +1,20 @@
 // Complex constrained TV denoising, problem (1), by Algorithm 2 (FGP).
 //
 // Kernels
-//   fgp_pass_kernel   T fused FGP iterations per launch on shared-memory tiles
-//                     (pass_tv.cuh; fgp_tile / fgp_strip_tile in ctv_device.cuh).
-//   fgp_gap_kernel    x = P_C(b - lam L^T q) (Eq. (18)) together with the primal
-//                     value of problem (1), the dual value of App. A (Eq. (30)
-//                     times lam) and their gap, reduced in FP64; its last block
-//                     applies the stopping test and, for the final call, writes
-//                     the statistics. Later passes read the stop flag and return.
+//   fgp_pass_kernel        T fused FGP iterations per launch on shared-memory tiles
+//                          (pass_tv.cuh; fgp_tile / fgp_strip_tile in ctv_device.cuh);
+//                          a pass that ends a check interval with fewer than T
+//                          iterations also adds up the duality-gap terms at its
+//                          final q (the gap-evaluating variant, pass_gap_tv*.cu).
+//   fgp_gap_kernel         x = P_C(b - lam L^T q) (Eq. (18)) together with the sums
+//                          of the primal value of problem (1) and of the dual value
+//                          of App. A (Eq. (30) times lam), per block into a slot.
+//   fgp_gap_finish_kernel  adds the slots of a check or of the final evaluation,
+//                          forms primal, dual and gap, applies the stopping test
+//                          and, for the final call, writes the statistics. Later
+//                          passes read the stop flag and return.
+//   fgp_finalize_kernel    x (and the exported q) only, for solves whose statistics
+//                          nobody reads.
 // Host entry points: ctv_denoise, ctv_denoise_batched (declared in ctv.h).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -29,148 +36,92 @@
 
 namespace ctv {
 
-// Duality gap / finalize evaluation streamed down bands of rows by warps
-// (Eq. (18), problem (1), App. A Eq. (30)). A warp's 32 lanes cover 32 adjacent
-// columns and it owns the 30 of lanes 1..30: x at a lane needs q one column to
-// the left (lane - 1, by shuffle) and the TV summand needs x one column to the
-// right (lane + 1). It walks a band of GS_H rows top to bottom, one row per step,
-// keeping the previous row's p1 (the upper neighbour of L^T q) and x (the upper
-// end of the vertical difference) in registers, and loads GS_D rows ahead into a
-// register ring so that loads are in flight while it computes. No shared-memory
-// tiles and no block barriers until the final reduction: one pass over b and q
-// (24 B per pixel, 32/30 of the columns), plus x (8 B) for the final call.
-// The three sums are kept per lane in compensated FP32 (Kahan) over the band,
-// reduced across the warp as FP32 pairs without rounding loss and only then
-// turned into FP64 - once per warp: this GPU's FP64 rate is a small fraction of
-// its FP32 rate, and FP64 additions per group of rows had taken a third of the
-// kernel's time. One set of FP64 atomics per block commits the block's sums.
-constexpr int GS_WARPS = 8, GS_NT = 32 * GS_WARPS, GS_OWN = 30, GS_H = 32, GS_D = 4;
-
-template <int TV, int CONS>
-__global__ void __launch_bounds__(GS_NT, 3) fgp_gap_kernel(GapParams p) {
-  __shared__ double wsum[3][GS_WARPS];
-  __shared__ int last;
+// Duality gap / finalize evaluation (Eq. (18), problem (1), App. A Eq. (30)) on
+// 64 x 16 tiles with a one-pixel halo (gap_tile_add): persistent blocks walk the
+// tiles of an image, keep the three sums in compensated FP32 and store the
+// block's sums, as FP32 pairs, in its slot; fgp_gap_finish_kernel evaluates
+// them. No FP64 arithmetic per block (this GPU's FP64 rate is a small fraction of
+// its FP32 rate) and no fence or atomic per block.
+template <int TV>
+__global__ void __launch_bounds__(GAP_NT, 4) fgp_gap_kernel(GapParams p) {
+  __shared__ float4 qs[GAP_RW * GAP_RH];
+  __shared__ float2 xs[GAP_RW * GAP_RH];
+  __shared__ float2 red[3 * (GAP_NT / 32)];
   const int z = blockIdx.z;
   DevStats* st = p.st + z;
   const int stopped = *(volatile int*)&st->stop;
   if (!p.final_call && stopped) return;
   const int set = stopped ? st->stop_set : p.default_set;
-  const int m = p.m, n = p.n;
-  const float2* b = p.b + z * p.b_stride;
+  GapImg g;
+  g.b = p.b + z * p.b_stride;
+  g.ld = p.ld;
   const bool zq = p.zero_q != 0 && !stopped;
-  const float4* q = zq ? nullptr : (set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in)) + z * p.d_stride;
-  float2* x_out = p.x != nullptr ? p.x + z * p.x_stride : nullptr;
-  float4* q_exp = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
+  const float4* q = set == 0 ? p.qA : (set == 1 ? p.qB : p.dual_in);
+  g.q = zq ? nullptr : q + z * p.d_stride;
+  g.x = p.x != nullptr ? p.x + z * p.x_stride : nullptr;
+  g.q_export = p.q_export != nullptr ? p.q_export + z * p.d_stride : nullptr;
+  g.m = p.m;
+  g.n = p.n;
   const float lv = p.lam_dev != nullptr ? p.lam_dev[z] : p.lam;
-  const bool bad_lam = !(lv >= 0.f);
-  const float lam = bad_lam ? 0.f : lv;
-  const float alpha = p.alpha;
-  const ConsDev C = p.C;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ncw = (n + GS_OWN - 1) / GS_OWN, nbr = (m + GS_H - 1) / GS_H;
-  const int g = blockIdx.x * GS_WARPS + warp;
-  float ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};   // compensated per-lane sums
+  g.lam = lv >= 0.f ? lv : 0.f;
+  g.alpha = p.alpha;
+  g.C = p.C;
+  GapSums acc = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, false};
   bool nf = false;
-  if (g < ncw * nbr) {   // warp-uniform
-    const int bc = g % ncw, br = g / ncw;
-    const int k = bc * GS_OWN - 1 + lane;
-    const bool kin = (unsigned)k < (unsigned)n;
-    const bool own = lane >= 1 && lane <= GS_OWN && kin;
-    const bool has_right = k < n - 1;
-    const bool kin_rect = k >= C.k0 && k < C.k1;   // column inside a support rectangle
-    const int jA = br * GS_H, jB = min(jA + GS_H, m);
-    const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-    float4 rq[GS_D];
-    float2 rb[GS_D];
-    auto load = [&](int j, float4& qv, float2& bv) {
-      qv = z4;
-      bv = make_float2(0.f, 0.f);
-      if (kin && (unsigned)j < (unsigned)m) {
-        if (q != nullptr) qv = __ldg(q + (long long)j * n + k);
-        bv = __ldg(b + (long long)j * p.ld + k);
-      }
-    };
-#pragma unroll
-    for (int u = 0; u < GS_D; ++u) load(jA - 1 + u, rq[u], rb[u]);
-    float2 p1u = make_float2(0.f, 0.f);   // p1 of the row above
-    float2 xu = make_float2(0.f, 0.f);    // x of the row above
-    // rows jA - 1 (its p1 only) to jB (its x only, for the vertical difference of row jB - 1);
-    // the ring slot of a row is a compile-time index (the rows are walked in groups of
-    // GS_D, the last group guarded rather than cut short)
-    for (int j0 = jA - 1; j0 <= jB; j0 += GS_D) {
-#pragma unroll
-      for (int u = 0; u < GS_D; ++u) {
-        const int j = j0 + u;
-        if (j <= jB) {   // warp-uniform, like every row test below
-          const float4 qc = rq[u];
-          const float2 bb = rb[u];
-          if (j + GS_D <= jB) load(j + GS_D, rq[u], rb[u]);
-          // p2 of the left neighbour from lane - 1 (lane 0's x is never used)
-          const float l2r = __shfl_up_sync(0xffffffffu, qc.z, 1);
-          const float l2i = __shfl_up_sync(0xffffffffu, qc.w, 1);
-          // x of the right neighbour in the row above, from lane + 1
-          const float xrr = __shfl_down_sync(0xffffffffu, xu.x, 1);
-          const float xri = __shfl_down_sync(0xffffffffu, xu.y, 1);
-          const bool row_in = j >= jA && j < m;
-          float2 xc = make_float2(0.f, 0.f);
-          float dlr = 0.f, dli = 0.f, wr = 0.f, wi = 0.f;
-          if (row_in) {
-            // (L^T q)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]; x = P_C(b - lam L^T q)
-            // with one fused multiply-add per part, as in every kernel that evaluates
-            // Eq. (18) at the end of a solve, so that all of them give the same bits
-            const float tr = qc.x - p1u.x + qc.z - l2r, ti = qc.y - p1u.y + qc.w - l2i;
-            xc = proj_C_t<CONS>(make_float2(fmaf(-lam, tr, bb.x), fmaf(-lam, ti, bb.y)), j, k, kin_rect, C);
-            dlr = lam * tr;
-            dli = lam * ti;
-            wr = bb.x - dlr;
-            wi = bb.y - dli;
-          }
-          if (own && j > jA) {
-            // TV summand of row j - 1: d1 = x[j-1,k] - x[j,k] (none on the last row),
-            // d2 = x[j-1,k] - x[j-1,k+1] (none on the last column)
-            const float d1r = j < m ? xu.x - xc.x : 0.f, d1i = j < m ? xu.y - xc.y : 0.f;
-            const float d2r = has_right ? xu.x - xrr : 0.f, d2i = has_right ? xu.y - xri : 0.f;
-            kahan_add(ks[1], kc[1], tv_term<TV>(d1r, d1i, d2r, d2i, alpha));
-          }
-          if (own && row_in && j < jB) {
-            nf |= nonfinite2(bb);
-            const float er = xc.x - bb.x, ei = xc.y - bb.y;
-            kahan_add(ks[0], kc[0], er * er + ei * ei);
-            // ||b||^2 - ||w||^2 = 2 <b, lam L^T q> - ||lam L^T q||^2, plus ||w - P_C(w)||^2
-            const float hr = wr - xc.x, hi = wi - xc.y;
-            kahan_add(ks[2], kc[2], (2.f * (bb.x * dlr + bb.y * dli) - (dlr * dlr + dli * dli)) + (hr * hr + hi * hi));
-            if (x_out != nullptr) x_out[(long long)j * p.ld + k] = xc;
-            if (q_exp != nullptr) q_exp[(long long)j * n + k] = qc;
-          }
-          xu = xc;
-          p1u = make_float2(qc.x, qc.y);
-        }
-      }
-    }
+  const int tx = (p.n + GAP_RW - 3) / (GAP_RW - 2), ty = (p.m + GAP_RH - 3) / (GAP_RH - 2);
+  for (int t = blockIdx.x; t < tx * ty; t += gridDim.x) {
+    const int by = t / tx, bx = t - by * tx;
+    gap_tile_add<TV>(g, by * (GAP_RH - 2), bx * (GAP_RW - 2), qs, xs, acc, nf);
+    __syncthreads();
   }
-  // the lane's sum is ks - kc; warp sums as FP32 pairs, then FP64 per warp
+  float hs[3], ls[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float hi = ks[a], lo = -kc[a];
-    warp_sum_pair(hi, lo);
-    if (lane == 0) wsum[a][warp] = (double)hi + (double)lo;
+    hs[a] = acc.s[a];
+    ls[a] = -acc.c[a];
   }
+  block_sum_pairs<GAP_NT, 3>(hs, ls, red);
   const bool block_nf = __syncthreads_or(nf) != 0;
   if (block_nf && threadIdx.x == 0) raise_async(CTV_ENONFINITE);
-  // (__syncthreads_or above also ordered the warps' wsum stores)
-  double acc[3] = {0.0, 0.0, 0.0};
+  gap_store_slot(st, p.slots + z * p.slot_stride, blockIdx.x, hs, ls, block_nf);
+}
+
+// Evaluation of a slot reduction, one block per image (see GapFinishParams).
+constexpr int GF_NT = 1024;
+__global__ void __launch_bounds__(GF_NT) fgp_gap_finish_kernel(GapFinishParams f) {
+  __shared__ float2 red[3 * (GF_NT / 32)];
+  const int z = blockIdx.x;
+  DevStats* st = f.st + z;
+  const int stopped = *(volatile int*)&st->stop;
+  if (!f.final_call && stopped) return;   // an earlier check stopped the solve; this one did not run
+  const float* slots = f.slots + z * f.slot_stride;
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (unsigned i = threadIdx.x; i < f.nblk; i += GF_NT) {
+    const float4* sl = reinterpret_cast<const float4*>(slots + 8 * (size_t)i);
+    const float4 a = sl[0], b = sl[1];
+    pair_add(h[0], l[0], a.x, a.y);
+    pair_add(h[1], l[1], a.z, a.w);
+    pair_add(h[2], l[2], b.x, b.y);
+  }
+  block_sum_pairs<GF_NT, 3>(h, l, red);
   if (threadIdx.x == 0) {
+    const float lv = f.lam_dev != nullptr ? f.lam_dev[z] : f.lam;
+    const bool bad_lam = !(lv >= 0.f);
+    gap_finish(st, (double)h[0] + (double)l[0], (double)h[1] + (double)l[1], (double)h[2] + (double)l[2],
+               bad_lam ? 0.f : lv, bad_lam, f.set, stopped, f.iter, f.gap_tol, f.final_call);
+    // inside a stop graph, the check that stops the solve skips the remaining intervals
+    if (f.n_cond > 0 && st->stop) {
 #pragma unroll
-    for (int w = 0; w < GS_WARPS; ++w) {
-      acc[0] += wsum[0][w];
-      acc[1] += wsum[1][w];
-      acc[2] += wsum[2][w];
+      for (int i = 0; i < CTV_MAX_STOP_INTERVALS; ++i)
+        if (i < f.n_cond) cudaGraphSetConditional(f.cond[i], 0u);
     }
   }
-  gap_commit(st, acc, gridDim.x, 1u, lam, bad_lam, set, stopped, p.iter, p.gap_tol, p.final_call, &last, block_nf);
-  // inside a stop graph, the check that stops the solve skips the remaining intervals
-  if (p.n_cond > 0 && threadIdx.x == 0 && last && st->stop)
-    for (int i = 0; i < p.n_cond; ++i) cudaGraphSetConditional(p.cond[i], 0u);
+}
+
+cudaError_t launch_gap_finish(const GapFinishParams& f, int batch, cudaStream_t s) {
+  fgp_gap_finish_kernel<<<batch, GF_NT, 0, s>>>(f);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
@@ -188,6 +139,16 @@ static const int kNumCfgs = (int)(sizeof(kCfgs) / sizeof(kCfgs[0]));
 cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStream_t s) {
   if (cfg < 0 || cfg >= kNumCfgs) return cudaErrorInvalidValue;
   const int cons = cons_mode(p.C);
+  if (p.gap_eval) {
+    if (!pass_gap_eval_ok(cfg)) return cudaErrorInvalidValue;
+    switch (tv) {
+      case TV1_ISO: return launch_pass_gap_tv<TV1_ISO>(cfg, cons, p, grid, s);
+      case TV1_ANISO: return launch_pass_gap_tv<TV1_ANISO>(cfg, cons, p, grid, s);
+      case TV2_ISO: return launch_pass_gap_tv<TV2_ISO>(cfg, cons, p, grid, s);
+      case TV2_ANISO: return launch_pass_gap_tv<TV2_ANISO>(cfg, cons, p, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (tv) {
     case TV1_ISO: return launch_pass_tv<TV1_ISO>(cfg, cons, p, grid, s);
     case TV1_ANISO: return launch_pass_tv<TV1_ANISO>(cfg, cons, p, grid, s);
@@ -195,6 +156,16 @@ cudaError_t launch_pass(int tv, int cfg, const PassParams& p, dim3 grid, cudaStr
     case TV2_ANISO: return launch_pass_tv<TV2_ANISO>(cfg, cons, p, grid, s);
   }
   return cudaErrorInvalidValue;
+}
+
+bool pass_gap_eval_ok(int cfg) {
+  switch (cfg) {
+#define CTV_GAP_OK(id, kind, T, A, B, C) \
+  case id: return GapEvalOk<kind, C>::value;
+    CTV_PASS_CONFIGS(CTV_GAP_OK)
+#undef CTV_GAP_OK
+  }
+  return false;
 }
 
 // x = P_C(b - lam L^T q) (Eq. (18)) and the optional export of q, without the
@@ -276,29 +247,42 @@ int occupancy_once(const void* kernel, int threads, int (&cached)[kMaxDevices]) 
 }
 
 template <int TV>
-static void launch_gap_tv(const GapParams& p, dim3 grid, cudaStream_t s) {
-  switch (cons_mode(p.C)) {
-    case CONS_NONE: fgp_gap_kernel<TV, CONS_NONE><<<grid, GS_NT, 0, s>>>(p); break;
-    case CONS_AMP: fgp_gap_kernel<TV, CONS_AMP><<<grid, GS_NT, 0, s>>>(p); break;
-    case CONS_RECT: fgp_gap_kernel<TV, CONS_RECT><<<grid, GS_NT, 0, s>>>(p); break;
-    default: fgp_gap_kernel<TV, CONS_GEN><<<grid, GS_NT, 0, s>>>(p); break;
-  }
+static long long launch_gap_tv(const GapParams& p, int batch, cudaStream_t s) {
+  static int per_sm_cache[kMaxDevices] = {};
+  const int per_sm = occupancy_once((const void*)fgp_gap_kernel<TV>, GAP_NT, per_sm_cache);
+  const long long tiles = (long long)((p.n + GAP_RW - 3) / (GAP_RW - 2)) * ((p.m + GAP_RH - 3) / (GAP_RH - 2));
+  const long long cap = (long long)per_sm * sm_count();
+  const long long blocks = tiles < cap ? tiles : cap;
+  fgp_gap_kernel<TV><<<dim3((unsigned)blocks, 1, batch), GAP_NT, 0, s>>>(p);
+  return blocks;
 }
 
 cudaError_t launch_gap(int tv, const GapParams& p, int batch, cudaStream_t s) {
-  // one warp per band of GS_H rows and GS_OWN columns
-  const long long warps = (long long)((p.n + GS_OWN - 1) / GS_OWN) * ((p.m + GS_H - 1) / GS_H);
-  const long long blocks = (warps + GS_WARPS - 1) / GS_WARPS;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)blocks, 1, batch);
+  long long blocks = 0;
   switch (tv) {
-    case TV1_ISO: launch_gap_tv<TV1_ISO>(p, grid, s); break;
-    case TV1_ANISO: launch_gap_tv<TV1_ANISO>(p, grid, s); break;
-    case TV2_ISO: launch_gap_tv<TV2_ISO>(p, grid, s); break;
-    case TV2_ANISO: launch_gap_tv<TV2_ANISO>(p, grid, s); break;
+    case TV1_ISO: blocks = launch_gap_tv<TV1_ISO>(p, batch, s); break;
+    case TV1_ANISO: blocks = launch_gap_tv<TV1_ANISO>(p, batch, s); break;
+    case TV2_ISO: blocks = launch_gap_tv<TV2_ISO>(p, batch, s); break;
+    case TV2_ANISO: blocks = launch_gap_tv<TV2_ANISO>(p, batch, s); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  GapFinishParams f;
+  memset(&f, 0, sizeof(f));
+  f.st = p.st;
+  f.slots = p.slots;
+  f.slot_stride = p.slot_stride;
+  f.nblk = (unsigned)blocks;
+  f.lam = p.lam;
+  f.lam_dev = p.lam_dev;
+  f.set = p.default_set;
+  f.iter = p.iter;
+  f.gap_tol = p.gap_tol;
+  f.final_call = p.final_call;
+  f.n_cond = p.n_cond;
+  for (int i = 0; i < p.n_cond; ++i) f.cond[i] = p.cond[i];
+  return launch_gap_finish(f, batch, s);
 }
 
 dim3 pass_grid(int cfg, int m, int n, int batch) {
@@ -307,7 +291,7 @@ dim3 pass_grid(int cfg, int m, int n, int batch) {
               batch);
 }
 
-int default_config(int m, int n, int iters, int tv) {
+int default_config(int m, int n, int iters, int tv, int cons) {
   if (m <= 0 || n <= 0) return 11;   // plans of many images (see plan.cu for the configurations they support)
   if (iters < 2) return 0;
   if (m > 0 && n > 0) {
@@ -315,25 +299,23 @@ int default_config(int m, int n, int iters, int tv) {
     if (t >= 0) return t;
   }
   // measured on GB300 (2048^2 to 256^2 phantoms, all four TV types): column-strip
-  // kernels; 4 iterations per 64 x 32 region, 4 rows per thread, two 512-thread
-  // blocks per SM at 2048^2; 6 per 64 x 64 region around 1024^2; below about
-  // 448^2, where too few regions fill the GPU, 32 x 32 regions with one row per
-  // thread (1024 threads) and 8 iterations per pass (15.5 against 10.5
-  // Gpixel-iter/s for 4 iterations at 128^2, 63 against 57 at 384^2; at 256^2
-  // the 4-iteration config 16 is 5% faster)
+  // kernels. Below about 448^2, where too few regions fill the GPU, 32 x 32 regions
+  // with one row per thread (two 1024-thread blocks per SM) and 8 iterations per
+  // pass; 6 iterations per 64 x 64 region up to about 1536^2. Above, with a
+  // support rectangle (whose outside tiles take the neighbour-free body) 6
+  // iterations per 64 x 64 region and 4 rows per thread (225.8 against 208.8
+  // Gpixel-iter/s for 4 per 64 x 32 at 2048^2), otherwise 6 iterations per 64 x 64
+  // region with 8 rows per thread (188.3 against 181.2).
   const double px = (double)m * (double)n;
   if (px < 448.0 * 448.0) return 17;
   if (px < 1536.0 * 1536.0) return 14;
-  return 11;
+  return cons == CONS_RECT ? 14 : 5;
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t denoise_workspace_bytes(int batch, int m, int n) {
-  if (batch <= 0 || m <= 0 || n <= 0) return 0;
-  const size_t px = (size_t)batch * m * n;
-  return align256((size_t)batch * sizeof(DevStats)) + 4 * align256(px * sizeof(float4));
-}
+static_assert(sizeof(DevStats) <= 256, "statistics record must fit its 256-byte slot");
+size_t denoise_workspace_bytes(int batch, int m, int n) { return denoise_workspace_bytes_c(batch, m, n); }
 
 bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out) {
   memset(out, 0, sizeof(*out));
@@ -562,16 +544,19 @@ ctv_status run_denoise(const DenoiseCall& c) {
   if (K < 0 || check_every < 0 || !(gap_tol >= 0.0) || !(alpha >= 0.f && alpha <= 1.f)) return CTV_EINVAL;
   if (warm && c.dual_state == nullptr) return CTV_EINVAL;
   if (cfg >= kNumCfgs || cfg < -1) return CTV_EINVAL;
-  if (cfg < 0) cfg = default_config(c.m, c.n, K, c.tv);
   ConsDev C;
   if (!convert_constraint(c.C, c.m, c.n, &C)) return CTV_EINVAL;
+  if (cfg < 0) cfg = default_config(c.m, c.n, K, c.tv, cons_mode(C));
   if (c.workspace_bytes < denoise_workspace_bytes(c.batch, c.m, c.n)) return CTV_EINVAL;
 
   cudaStream_t s = (cudaStream_t)c.stream;
   const size_t px = (size_t)c.m * c.n;
   char* ws = (char*)c.workspace;
   DevStats* st = (DevStats*)ws;
-  size_t off = align256((size_t)c.batch * sizeof(DevStats));
+  size_t off = align256((size_t)c.batch * 256);
+  float* slots = (float*)(ws + off);
+  const long long slot_stride = 8 * (long long)gap_slots_per_image(c.m, c.n);
+  off += align256((size_t)c.batch * gap_slots_per_image(c.m, c.n) * 32);
   float4* set_q[2];
   float4* set_r[2];
   const size_t dbytes = align256((size_t)c.batch * px * sizeof(float4));
@@ -600,6 +585,8 @@ ctv_status run_denoise(const DenoiseCall& c) {
   g.alpha = alpha;
   g.C = C;
   g.st = st;
+  g.slots = slots;
+  g.slot_stride = slot_stride;
   g.gap_tol = gap_tol;
 
   // the passes, checks and finalize of the solve, onto stream es, or (sg != nullptr) into a
@@ -662,21 +649,60 @@ ctv_status run_denoise(const DenoiseCall& c) {
         p.q_out = set_q[out];
         p.r_out = set_r[out];
         const double units = (double)c.batch * (double)px * (double)steps;
-        const int slot = pmode == 1 ? prof_begin(es) : -1;
-        if (pmode == 2 && run_slot < 0) run_slot = prof_begin(es);
+        // A check after this pass is evaluated inside it when it runs fewer than T steps
+        // (then q_k is exact one ring beyond the tile interiors, all the gap terms need).
+        const bool check_after = check_every > 0 && (k + steps - 1) % check_every == 0 && k + steps - 1 < K;
+        const bool fused_check = check_after && steps < cf.T && pass_gap_eval_ok(cfg) &&
+                                 (size_t)grid.x * grid.y <= gap_slots_per_image(c.m, c.n);
+        p.gap_eval = fused_check ? 1 : 0;
+        if (fused_check) {
+          p.gst = st;
+          p.slots = slots;
+          p.slot_stride = slot_stride;
+          close_run(es);   // (timing runs cover plain passes only)
+        }
+        const int slot = pmode == 1 && !fused_check ? prof_begin(es) : -1;
+        if (pmode == 2 && run_slot < 0 && !fused_check) run_slot = prof_begin(es);
         if (launch_pass(c.tv, cfg, p, grid, es) != cudaSuccess) return CTV_ECUDA;
         count_launch();
         if (sg != nullptr) sg->kernels++;
         prof_end(slot, es, units, 1);
-        run_units += units;
-        ++run_n;
+        if (!fused_check) {
+          run_units += units;
+          ++run_n;
+        }
         first = false;
         k += steps;
         last_set = out;
         q_in = set_q[out];
         r_in = set_r[out];
         out ^= 1;
-        if (check_every > 0 && (k - 1) % check_every == 0 && k - 1 < K) {
+        if (fused_check) {
+          // the passes' block sums, evaluated and tested by one block per image
+          GapFinishParams f;
+          memset(&f, 0, sizeof(f));
+          f.st = st;
+          f.slots = slots;
+          f.slot_stride = slot_stride;
+          f.nblk = grid.x * grid.y;
+          f.lam = c.lam;
+          f.lam_dev = c.lam_dev;
+          f.set = last_set;
+          f.iter = k - 1;
+          f.gap_tol = gap_tol;
+          f.final_call = 0;
+          if (sg != nullptr) {
+            sg->later_handles(&gg);
+            f.n_cond = gg.n_cond;
+            for (int i = 0; i < gg.n_cond; ++i) f.cond[i] = gg.cond[i];
+          }
+          if (launch_gap_finish(f, c.batch, es) != cudaSuccess) return CTV_ECUDA;
+          count_launch();
+          if (sg != nullptr) {
+            sg->kernels++;
+            if (!sg->close_interval()) return CTV_ECUDA;
+          }
+        } else if (check_after) {
           close_run(es);
           gg.default_set = last_set;
           gg.zero_q = 0;
@@ -687,9 +713,9 @@ ctv_status run_denoise(const DenoiseCall& c) {
           if (sg != nullptr) sg->later_handles(&gg);
           else gg.n_cond = 0;
           if (launch_gap(c.tv, gg, c.batch, es) != cudaSuccess) return CTV_ECUDA;
-          count_launch();
+          count_launches(2);
           if (sg != nullptr) {
-            sg->kernels++;
+            sg->kernels += 2;
             if (!sg->close_interval()) return CTV_ECUDA;
           }
         }
@@ -723,9 +749,9 @@ ctv_status run_denoise(const DenoiseCall& c) {
     const bool light = c.stats == nullptr && check_every == 0;
     if ((light ? launch_finalize(gg, c.batch, es) : launch_gap(c.tv, gg, c.batch, es)) != cudaSuccess)
       return CTV_ECUDA;
-    count_launch();
+    count_launches(light ? 1 : 2);
     if (sg != nullptr) {
-      sg->kernels++;
+      sg->kernels += light ? 1 : 2;
       if (!sg->close_final()) return CTV_ECUDA;
     }
     return CTV_OK;
@@ -856,7 +882,11 @@ int ctv_denoise_batched(const void* b, void* x, int batch, int m, int n, int ld,
 
 int ctv_num_configs(void) { return ctv::num_configs(); }
 
-int ctv_default_config(int m, int n, int iters, int tv_type) { return ctv::default_config(m, n, iters, tv_type); }
+int ctv_default_config(int m, int n, int iters, int tv_type, const ctv_constraint* C) {
+  ctv::ConsDev cd;
+  if (!ctv::convert_constraint(C, m, n, &cd)) return -1;
+  return ctv::default_config(m, n, iters, tv_type, ctv::cons_mode(cd));
+}
 
 int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads) {
   return ctv::config_info(config, iters_per_pass, region_w, region_h, threads) ? CTV_OK : CTV_EINVAL;

@@ -28,12 +28,13 @@ constexpr int GAP_RW = 64, GAP_RH = 16, GAP_NT = 256;
 // needs x below and to the right. Returns, in thread 0, the block's sums of
 //   acc[0] = ||x - b||^2, acc[1] = TV(x), acc[2] = ||b||^2 - ||w||^2 + ||w - P_C(w)||^2
 // (w = b - lam L^T q), i.e. 2 P - 2 lam TV and 2 D of App. A.
-// gap_tile_add adds this thread's share of the three sums into acc (no block
-// reduction; the caller synchronises before reusing qs and xs) and sets nf when
-// one of the thread's values of b is a NaN or an infinity.
+// gap_tile_add adds this thread's share of the three sums (FP32 over its pixels
+// of the tile) into the compensated sums acc (no block reduction; the caller
+// synchronises before reusing qs and xs) and sets nf when one of the thread's
+// values of b is a NaN or an infinity.
 template <int TV>
 __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, float4* qs, float2* xs,
-                                             double (&acc)[3], bool& nf) {
+                                             GapSums& acc, bool& nf) {
   constexpr int RW = GAP_RW, RH = GAP_RH, NT = GAP_NT, R = RW * RH, PPT = R / NT;
   const int m = g.m, n = g.n;
   const int gj0 = j0 - 1, gk0 = k0 - 1;
@@ -102,16 +103,41 @@ __device__ __forceinline__ void gap_tile_add(const GapImg& g, int j0, int k0, fl
       if (g.q_export != nullptr) g.q_export[(long long)gj * n + gk] = qc;
     }
   }
-  acc[0] += (double)fa0;
-  acc[1] += (double)fa1;
-  acc[2] += (double)fa2;
+  kahan_add(acc.s[0], acc.c[0], fa0);
+  kahan_add(acc.s[1], acc.c[1], fa1);
+  kahan_add(acc.s[2], acc.c[2], fa2);
+}
+
+// Turns the three sums of a completed reduction into primal, dual and gap
+// (P = 1/2 ||x - b||^2 + lam TV(x), D = 1/2 (||b||^2 - ||w||^2 + ||w - P_C(w)||^2)),
+// applies the stopping test (checks) or records the final iteration count.
+__device__ __forceinline__ void gap_finish(DevStats* st, double fid, double tvs, double dual2, float lam,
+                                           bool bad_lam, int set, int stopped, int iter, double gap_tol,
+                                           int final_call) {
+  const double P = 0.5 * fid + (double)lam * tvs;
+  const double D = 0.5 * dual2;
+  st->primal = P;
+  st->dual = D;
+  st->gap = P - D;
+  if (bad_lam) st->status = 1;   // CTV_EINVAL
+  if (*(volatile unsigned int*)&st->nonfinite) st->status = 5;   // CTV_ENONFINITE
+  if (!final_call) {
+    st->iters = iter;
+    if (gap_tol > 0.0 && P - D <= gap_tol * fmax(P, 1e-30)) {
+      st->stop = 1;
+      st->stop_set = set;
+      st->stop_iter = iter;
+    }
+  } else {
+    st->iters = stopped ? st->stop_iter : iter;
+  }
 }
 
 // Adds the block sums into st and lets the commit that completes the reduction
-// (nblk units in all; this one covers `units` of them) turn them into primal,
-// dual and gap, apply the stopping test (checks) or record the final iteration
-// count, and reset the accumulators. Thread 0 holds the block sums; nonfinite
-// (any thread's flag, block-reduced by the caller) marks the image's record.
+// (nblk units in all; this one covers `units` of them) evaluate it and reset the
+// accumulators. Thread 0 holds the block sums; nonfinite (any thread's flag,
+// block-reduced by the caller) marks the image's record. FP64 atomics on one
+// address: for reductions with few commits per image (batched plans).
 __device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3], unsigned nblk, unsigned units,
                                            float lam, bool bad_lam, int set, int stopped, int iter, double gap_tol,
                                            int final_call, int* last, bool nonfinite) {
@@ -127,29 +153,30 @@ __device__ __forceinline__ void gap_commit(DevStats* st, const double (&acc)[3],
   if (*last && threadIdx.x == 0) {
     __threadfence();
     volatile double* a = st->acc;
-    const double fid = a[0], tvs = a[1], dual2 = a[2];
-    const double P = 0.5 * fid + (double)lam * tvs;
-    const double D = 0.5 * dual2;
-    st->primal = P;
-    st->dual = D;
-    st->gap = P - D;
-    if (bad_lam) st->status = 1;   // CTV_EINVAL
-    if (*(volatile unsigned int*)&st->nonfinite) st->status = 5;   // CTV_ENONFINITE
-    if (!final_call) {
-      st->iters = iter;
-      if (gap_tol > 0.0 && P - D <= gap_tol * fmax(P, 1e-30)) {
-        st->stop = 1;
-        st->stop_set = set;
-        st->stop_iter = iter;
-      }
-    } else {
-      st->iters = stopped ? st->stop_iter : iter;
-    }
+    gap_finish(st, a[0], a[1], a[2], lam, bad_lam, set, stopped, iter, gap_tol, final_call);
     a[0] = 0.0;
     a[1] = 0.0;
     a[2] = 0.0;
     __threadfence();
     st->blocks_done = 0u;
+  }
+}
+
+// For reductions over thousands of blocks: every block stores its sums - FP32
+// pairs (hi, lo) summed without rounding loss - in its own slot (8 floats at
+// slots + 8 blk), with no fence and no atomic, and a one-block kernel launched
+// after the reduction (fgp_gap_finish_kernel) adds all slots, always in the same
+// order, in FP32 pairs and evaluates them. A per-block memory fence and ticket
+// atomic at the end of every block would put their latency on each wave's
+// critical path, and FP64 work per block is slow on this GPU (its FP64 rate is a
+// small fraction of its FP32 rate). Thread 0 holds the block's pairs.
+__device__ __forceinline__ void gap_store_slot(DevStats* st, float* slots, unsigned blk, const float (&hi)[3],
+                                               const float (&lo)[3], bool nonfinite) {
+  if (threadIdx.x == 0) {
+    if (nonfinite) atomicOr(&st->nonfinite, 1u);
+    float4* sl = reinterpret_cast<float4*>(slots + 8 * (size_t)blk);
+    sl[0] = make_float4(hi[0], lo[0], hi[1], lo[1]);
+    sl[1] = make_float4(hi[2], lo[2], 0.f, 0.f);
   }
 }
 

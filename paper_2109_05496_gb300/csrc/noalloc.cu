@@ -27,8 +27,10 @@
 
 namespace {
 
-// statistics record (rounded up to 256 B) + two sets of (q, r), float4 per pixel
-constexpr size_t kNoAllocScratchBytes = 256 + 4 * sizeof(float4) * (size_t)CTV_NOALLOC_MAX_PIXELS;
+// the workspace of the largest accepted image: the statistics record, the slots
+// of the gap reduction and two sets of (q, r), float4 per pixel (every m x n with
+// m n <= CTV_NOALLOC_MAX_PIXELS needs at most this much)
+constexpr size_t kNoAllocScratchBytes = ctv::denoise_workspace_bytes_c(1, 512, 512) + 64 * 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -40,7 +42,6 @@ ctv_status scratch_for_current_device(void** out) {
   return CTV_OK;
 }
 
-static_assert(sizeof(ctv::DevStats) <= 256, "statistics record must fit its 256-byte slot");
 
 }  // namespace
 

@@ -17,7 +17,7 @@ namespace ctv {
 #define CTV_PDL 1
 #endif
 
-template <int KIND, int TV, int T, int A, int B, int C, int CONS>
+template <int KIND, int TV, int T, int A, int B, int C, int CONS, bool GAPEV>
 __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B, C>::MINB)
     fgp_pass_kernel(PassParams p) {
   using G = CfgGeom<KIND, A, B, C>;
@@ -46,15 +46,34 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B
   I.C = p.C;
   I.r_hist = nullptr;
   I.hist_plane = 0;
-  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
-                                              p.nsteps, p.first != 0);
+  if constexpr (!GAPEV) {
+    run_tile<KIND, TV, T, A, B, C, false, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T),
+                                                p.beta, p.nsteps, p.first != 0);
+  } else {
+    GapSums gs = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, false};
+    run_tile<KIND, TV, T, A, B, C, false, CONS, true>(I, blockIdx.y * (G::RH - 2 * T),
+                                                      blockIdx.x * (G::RW - 2 * T), p.beta, p.nsteps,
+                                                      p.first != 0, &gs);
+    // the block's sums as FP32 pairs into its slot (fgp_gap_finish_kernel, launched
+    // after this pass, evaluates them)
+    __shared__ float2 red[3 * (G::NT / 32)];
+    float hs[3], ls[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      hs[a] = gs.s[a];
+      ls[a] = -gs.c[a];
+    }
+    block_sum_pairs<G::NT, 3>(hs, ls, red);
+    const bool block_nf = __syncthreads_or(gs.nf) != 0;
+    gap_store_slot(p.gst + z, p.slots + z * p.slot_stride, blockIdx.y * gridDim.x + blockIdx.x, hs, ls, block_nf);
+  }
 }
 
-template <int KIND, int TV, int T, int A, int B, int C, int CONS>
+template <int KIND, int TV, int T, int A, int B, int C, int CONS, bool GAPEV>
 static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
   using G = CfgGeom<KIND, A, B, C>;
   static bool attr_done[kMaxDevices] = {};
-  cudaError_t e = smem_attr_once(fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>, G::SMEM, attr_done);
+  cudaError_t e = smem_attr_once(fgp_pass_kernel<KIND, TV, T, A, B, C, CONS, GAPEV>, G::SMEM, attr_done);
   if (e != cudaSuccess) return e;
 #if CTV_PDL
   cudaLaunchConfig_t lc;
@@ -68,25 +87,30 @@ static cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s)
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, fgp_pass_kernel<KIND, TV, T, A, B, C, CONS>, p);
+  return cudaLaunchKernelEx(&lc, fgp_pass_kernel<KIND, TV, T, A, B, C, CONS, GAPEV>, p);
 #else
-  fgp_pass_kernel<KIND, TV, T, A, B, C, CONS><<<grid, G::NT, G::SMEM, s>>>(p);
+  fgp_pass_kernel<KIND, TV, T, A, B, C, CONS, GAPEV><<<grid, G::NT, G::SMEM, s>>>(p);
   return cudaGetLastError();
 #endif
 }
 
 // Region kernels (kind 0) use the general constraint path; column-strip kernels
 // (kind 1) are specialised per constraint kind.
-template <int KIND, int TV, int T, int A, int B, int C>
+template <int KIND, int TV, int T, int A, int B, int C, bool GAPEV>
 static cudaError_t launch_pass_cons(int cons, const PassParams& p, dim3 grid, cudaStream_t s) {
   if constexpr (KIND == 0) {
-    return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, s);
+    if constexpr (GAPEV) return cudaErrorInvalidValue;
+    else return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN, false>(p, grid, s);
   } else {
-    switch (cons) {
-      case CONS_NONE: return launch_pass_t<KIND, TV, T, A, B, C, CONS_NONE>(p, grid, s);
-      case CONS_AMP: return launch_pass_t<KIND, TV, T, A, B, C, CONS_AMP>(p, grid, s);
-      case CONS_RECT: return launch_pass_t<KIND, TV, T, A, B, C, CONS_RECT>(p, grid, s);
-      default: return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN>(p, grid, s);
+    if constexpr (GAPEV && !GapEvalOk<KIND, C>::value) {
+      return cudaErrorInvalidValue;
+    } else {
+      switch (cons) {
+        case CONS_NONE: return launch_pass_t<KIND, TV, T, A, B, C, CONS_NONE, GAPEV>(p, grid, s);
+        case CONS_AMP: return launch_pass_t<KIND, TV, T, A, B, C, CONS_AMP, GAPEV>(p, grid, s);
+        case CONS_RECT: return launch_pass_t<KIND, TV, T, A, B, C, CONS_RECT, GAPEV>(p, grid, s);
+        default: return launch_pass_t<KIND, TV, T, A, B, C, CONS_GEN, GAPEV>(p, grid, s);
+      }
     }
   }
 }
@@ -95,7 +119,18 @@ template <int TV>
 cudaError_t launch_pass_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s) {
   switch (cfg) {
 #define CTV_CFG_CASE(id, kind, T, A, B, C) \
-  case id: return launch_pass_cons<kind, TV, T, A, B, C>(cons, p, grid, s);
+  case id: return launch_pass_cons<kind, TV, T, A, B, C, false>(cons, p, grid, s);
+    CTV_PASS_CONFIGS(CTV_CFG_CASE)
+#undef CTV_CFG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int TV>
+cudaError_t launch_pass_gap_tv(int cfg, int cons, const PassParams& p, dim3 grid, cudaStream_t s) {
+  switch (cfg) {
+#define CTV_CFG_CASE(id, kind, T, A, B, C) \
+  case id: return launch_pass_cons<kind, TV, T, A, B, C, true>(cons, p, grid, s);
     CTV_PASS_CONFIGS(CTV_CFG_CASE)
 #undef CTV_CFG_CASE
   }

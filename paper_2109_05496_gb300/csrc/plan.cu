@@ -106,14 +106,21 @@ struct ListGapParams {
   int final_call;
 };
 
-__device__ __forceinline__ void list_gap_commit(const PlanImg* d, double (&acc)[3], double* red, unsigned units,
+__device__ __forceinline__ void list_gap_commit(const PlanImg* d, GapSums& gsum, float2* red, unsigned units,
                                                 int set, int stopped, int iter, double gap_tol, int final_call,
                                                 int* last, bool& nf) {
   const bool block_nf = __syncthreads_or(nf) != 0;
   if (block_nf && threadIdx.x == 0) raise_async(CTV_ENONFINITE);
-  block_sum<GAP_NT, 3>(acc, red);
+  float hs[3], ls[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hs[a] = gsum.s[a];
+    ls[a] = -gsum.c[a];
+    gsum.s[a] = gsum.c[a] = 0.f;
+  }
+  block_sum_pairs<GAP_NT, 3>(hs, ls, red);
+  const double acc[3] = {(double)hs[0] + (double)ls[0], (double)hs[1] + (double)ls[1], (double)hs[2] + (double)ls[2]};
   gap_commit(d->st, acc, d->gnblk, units, d->lam, false, set, stopped, iter, gap_tol, final_call, last, block_nf);
-  acc[0] = acc[1] = acc[2] = 0.0;
   nf = false;
 }
 
@@ -125,11 +132,11 @@ __device__ __forceinline__ void list_gap_commit(const PlanImg* d, double (&acc)[
 __global__ void __launch_bounds__(GAP_NT, 4) fgp_gap_list_kernel(ListGapParams p) {
   __shared__ float4 qs[GAP_RW * GAP_RH];
   __shared__ float2 xs[GAP_RW * GAP_RH];
-  __shared__ double red[3 * (GAP_NT / 32)];
+  __shared__ float2 red[3 * (GAP_NT / 32)];
   __shared__ int last;
   const int per = (p.n_items + (int)gridDim.x - 1) / (int)gridDim.x;
   const int i0 = (int)blockIdx.x * per, i1 = min(i0 + per, p.n_items);
-  double acc[3] = {0.0, 0.0, 0.0};
+  GapSums acc = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, false};
   bool nf = false;
   int cur = -1, cur_set = 0, cur_stopped = 0;
   unsigned units = 0;
@@ -412,7 +419,7 @@ int ctv_plan_create(const ctv_image_desc* descs, int count, const ctv_opts* opts
   }
   int cfg = opts->config;
   if (cfg < -1 || cfg >= num_configs()) return CTV_EINVAL;
-  if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1);
+  if (cfg < 0) cfg = default_config(0, 0, opts->max_iters, -1, CONS_AMP);
   if (!plan_config_ok(cfg)) return CTV_EUNSUPPORTED;
   int T = 1, RW = 0, RH = 0, NT = 0;
   config_info(cfg, &T, &RW, &RH, &NT);

@@ -70,11 +70,17 @@ def test_tune_table_host_only(lib):
     before = v.value
     assert lib.ctv_tune_set(20, 1, 3) == 0
     assert lib.ctv_tune_get(20, 1, ctypes.byref(v)) == 0 and v.value == 3
-    assert lib.ctv_default_config(1024, 1024, 100, 1) == 3      # the tuned choice wins
+    assert lib.ctv_default_config(1024, 1024, 100, 1, None) == 3      # the tuned choice wins
     assert lib.ctv_tune_set(20, 1, before) == 0
     assert lib.ctv_tune_set(20, 9, 3) == 1 and lib.ctv_tune_set(99, 0, 3) == 1   # CTV_EINVAL
     assert lib.ctv_tune_set(20, 1, lib.ctv_num_configs()) == 1
-    assert lib.ctv_default_config(2048, 2048, 1, 0) == 0        # a single iteration needs no blocking
+    assert lib.ctv_default_config(2048, 2048, 1, 0, None) == 0        # a single iteration needs no blocking
+    # a support rectangle changes the large-image choice (its outside tiles are cheap)
+    from paper_2109_05496_gb300 import api
+    rect, _ = api.Constraint(amp_max=1.0, rect=(256, 256, 1792, 1792)).to_c()
+    amp, _ = api.Constraint(amp_max=1.0).to_c()
+    assert lib.ctv_default_config(2048, 2048, 200, 0, ctypes.byref(rect)) == 14
+    assert lib.ctv_default_config(2048, 2048, 200, 0, ctypes.byref(amp)) == 5
 
 
 def test_config_table_matches_library(lib):

@@ -166,13 +166,20 @@ def test_dual_export_and_warm_start(tv):
 
 
 # --------------------------------------------------------------- gap stopping
+# A check whose interval ends in a pass of fewer than T iterations is evaluated in
+# that pass (strip configurations of up to four rows per thread); otherwise, or
+# for other configurations, by the separate gap kernel after the pass. The cases
+# below run both: every = 10 ends its intervals in a short pass for T = 3, 4, 6, 8;
+# every = 12 is a multiple of T = 3, 4, 6 (separate kernel) but not of 8.
 @pytest.mark.parametrize("tv", ["tv1_iso", "tv2_aniso"])
-def test_gap_stopping(tv):
+@pytest.mark.parametrize("config,every", [(-1, 10), (11, 10), (11, 12), (14, 10), (14, 12), (7, 10), (7, 12),
+                                          (16, 10), (17, 12), (5, 10)])
+def test_gap_stopping(tv, config, every):
     m, n = 96, 80
     _, noisy = noisy_phantom(m, n, 0.1, seed=21)
     Cg, Co = cons_pair("amp_rect", m, n)
-    tol, every = 2e-4, 10
-    x, st = gpu_denoise(noisy, 0.05, 400, tv, 0.5, Cg, check_every=every, gap_tol=tol)
+    tol = 2e-4
+    x, st = gpu_denoise(noisy, 0.05, 400, tv, 0.5, Cg, check_every=every, gap_tol=tol, config=config)
     assert st["stopped"] and st["iters"] % every == 0 and 0 < st["iters"] < 400
     k = st["iters"]
     b, res = run_oracle(noisy, 0.05, k, tv, 0.5, Co, check_every=every)

@@ -15,9 +15,10 @@ import pytest
 
 from paper_2109_05496_gb300 import build
 
-UNITS = ("plan.cu", "pass_tv1.cu", "backward.cu", "denoise.cu")
+UNITS = ("plan.cu", "pass_tv1.cu", "pass_gap_tv1.cu", "backward.cu", "denoise.cu")
 KERNELS = ("fgp_pass_kernel", "fgp_pass_list_kernel", "fgp_hist_pass_kernel", "adj_stream_kernel",
-           "adj2_stream_kernel", "fgp_gap_kernel", "fgp_gap_list_kernel", "fgp_finalize_kernel")
+           "adj2_stream_kernel", "fgp_gap_kernel", "fgp_gap_list_kernel", "fgp_finalize_kernel",
+           "fgp_gap_finish_kernel")
 
 
 def _ptxas_report(unit, out_dir):
