@@ -14,6 +14,21 @@ from tests.helpers import TV_NAMES, f32, oracle_constraint
 
 pytestmark = pytest.mark.gpu
 
+# Gradients of the unrolled iteration are those of a piecewise smooth map: where a
+# projection (P_S, P_C) switches branch within the rounding error of the forward
+# iterates, the FP32 and FP64 sweeps differentiate different pieces and their
+# gradients differ by O(1) there (the FP64 oracle's own gradient moves by 0.3% of
+# its largest entry under an input change of 1e-7 on a 128^2 image, 50
+# iterations, TV1 anisotropic). Small seeded inputs below stay away from kinks:
+# bar 1e-4, 25x the largest difference measured on them. On the full-size
+# 8 x 1024^2 workload some pixel always sits near a kink; there the oracle's own
+# lambda-gradient moves by 1.2-2.9% (and its derivative along a random input
+# direction by 0.5-1.6%) under a 1e-6 relative input change, the size of the
+# FP32 forward error after 50 iterations, while the GPU agreed within 6.3e-5 and
+# 8.7e-4: bar 2e-3.
+GRAD_TOL = 1e-4
+FULL_SIZE_GRAD_TOL = 2e-3
+
 
 def oracle_grads(b_np, lams, K, tv, alpha, Co, xbar_np):
     """d<xbar, x>/db and d<xbar, x>/dlam of the oracle in FP64, per image."""
@@ -67,8 +82,11 @@ def test_unrolled_gradient_matches_oracle(tv, kind):
     _, gb, gl = gpu_grads(imgs, lams, K, tv, 0.5, C, xbar, ckpt)
     ob, ol = oracle_grads(imgs, lams, K, tv, 0.5, Co, xbar)
     scale = np.abs(ob).max()
-    assert np.abs(gb - ob).max() <= 2e-3 * scale, np.abs(gb - ob).max() / scale
-    np.testing.assert_allclose(gl, ol, rtol=2e-3, atol=2e-3 * np.abs(ol).max())
+    # GRAD_TOL: away from the projections' kinks the FP32 reverse sweep agrees with
+    # the FP64 one to about 5e-7 of the largest entry (dL/db) and 4e-6 (dL/dlambda)
+    # on these inputs; see the module docstring for inputs near a kink
+    assert np.abs(gb - ob).max() <= GRAD_TOL * scale, np.abs(gb - ob).max() / scale
+    np.testing.assert_allclose(gl, ol, rtol=GRAD_TOL, atol=GRAD_TOL * np.abs(ol).max())
 
 
 @pytest.mark.parametrize("ckpt", [1, 3, 10, 50])
@@ -121,6 +139,8 @@ def test_finite_differences_fp64_32x32(tv):
     gb = b.grad.cpu().numpy()[0].astype(np.complex128)
     bc = torch.tensor(b_np[0].astype(np.complex128))
     rng = np.random.default_rng(2)
+    # central differences of step h = 1e-6 in FP64: the bar (2e-3, relative to
+    # max(1, |fd|)) leaves room for a difference whose interval crosses a kink
     h = 1e-6
     for _ in range(3):
         d = torch.tensor(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))
@@ -151,7 +171,7 @@ def test_full_size_gradient_window():
                              xbar[i:i + 1, j0:j1, k0:k1])
         want = ob[0, j - j0, k - k0]
         scale = np.abs(ob).max()
-        assert abs(gb[i, j, k] - want) <= 2e-3 * scale
+        assert abs(gb[i, j, k] - want) <= FULL_SIZE_GRAD_TOL * scale
 
 
 def _oracle_forward_derivative(b_np, lam, K, tv, alpha, Co, xbar_np, db=None):
@@ -188,8 +208,8 @@ def test_full_size_lambda_gradient_and_directional_derivative():
     _, gb, gl = gpu_grads(imgs, lams, K, "tv1_iso", 0.5, C, xbar, 10)
     for i in (1, 6):
         want = _oracle_forward_derivative(imgs[i], lams[i], K, "tv1_iso", 0.5, Co, xbar[i])
-        assert abs(gl[i] - want) <= 2e-3 * abs(want), (gl[i], want)
+        assert abs(gl[i] - want) <= FULL_SIZE_GRAD_TOL * abs(want), (gl[i], want)
         d = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
         want_b = _oracle_forward_derivative(imgs[i], lams[i], K, "tv1_iso", 0.5, Co, xbar[i], db=d)
         got_b = float((gb[i].real.astype(np.float64) * d.real + gb[i].imag.astype(np.float64) * d.imag).sum())
-        assert abs(got_b - want_b) <= 2e-3 * abs(want_b), (got_b, want_b)
+        assert abs(got_b - want_b) <= FULL_SIZE_GRAD_TOL * abs(want_b), (got_b, want_b)
