@@ -145,8 +145,10 @@ int ctv_get_last_error(ctv_stream stream);
 int ctv_num_configs(void);
 int ctv_config_info(int config, int* iters_per_pass, int* region_w, int* region_h, int* threads);
 /* The configuration that opts->config = -1 selects for an m x n image, K
- * iterations, a TV type and the set C (NULL: no constraint) - the autotuned
- * choice when there is one. -1 if C is invalid. */
+ * iterations, a TV type and the set C (NULL: no constraint) in a solve without
+ * gap checks - the autotuned choice when there is one. (With gap checks an
+ * untuned choice of 8 iterations per pass moves to the same region with 6 where
+ * that needs no more passes per check interval.) -1 if C is invalid. */
 int ctv_default_config(int m, int n, int iters, int tv_type, const ctv_constraint* C);
 
 /* Autotuner (no counterpart in the paper). ctv_autotune_denoise runs
@@ -228,7 +230,7 @@ int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lamb
  * Batched denoising of many images of uneven sizes (problem (1) per image).
  * Each image has its own shape, lambda, alpha, TV type and C; all share
  * opts->max_iters, check_every and gap_tol (warm_start must be 0; config -1
- * picks one; plans support configurations 2, 7, 11 and 14, others return
+ * picks 6; plans support configurations 2, 5, 6, 7, 11, 14 and 18, others return
  * CTV_EUNSUPPORTED; CTV_CONFIG_AUTOTUNE makes ctv_plan_create build a plan in
  * each supported configuration in turn, time one execution of it after a
  * warm-up on the caller's images (writing their x, synchronising), and keep the fastest -

@@ -27,7 +27,8 @@
   X(14, 1, 6, 2, 16, 4)      \
   X(15, 1, 4, 1, 16, 2)      \
   X(16, 1, 4, 1, 32, 1)      \
-  X(17, 1, 8, 1, 32, 1)
+  X(17, 1, 8, 1, 32, 1)      \
+  X(18, 1, 8, 2, 16, 4)
 
 namespace ctv {
 

@@ -69,7 +69,9 @@ constexpr size_t denoise_workspace_bytes_c(int batch, int m, int n) {
 bool convert_constraint(const ctv_constraint* C, int m, int n, ConsDev* out);
 void nesterov_betas(int K, std::vector<double>* beta);
 // cons: the constraint specialisation (CONS_*) of the solve's C
-int default_config(int m, int n, int iters, int tv, int cons);
+// check_every: the solve's gap-check interval (0: none), which can change the
+// best iterations per pass
+int default_config(int m, int n, int iters, int tv, int cons, int check_every = 0);
 int tuned_config(int m, int n, int tv);   // -1 when the size class / TV type is not tuned
 int size_class(int m, int n);
 int num_configs();

@@ -291,25 +291,47 @@ dim3 pass_grid(int cfg, int m, int n, int batch) {
               batch);
 }
 
-int default_config(int m, int n, int iters, int tv, int cons) {
-  if (m <= 0 || n <= 0) return 11;   // plans of many images (see plan.cu for the configurations they support)
+int default_config(int m, int n, int iters, int tv, int cons, int check_every) {
+  // plans of many images (plan_list.cuh lists the configurations they support):
+  // 64 x 64 regions of 8 iterations with 8 rows per thread (151.6 Gpixel-iter/s
+  // on 512 images of sides 64 to 1024 against 143.1 for 6 iterations and 4 rows)
+  if (m <= 0 || n <= 0) return 6;
   if (iters < 2) return 0;
   if (m > 0 && n > 0) {
     const int t = tuned_config(m, n, tv);
     if (t >= 0) return t;
   }
-  // measured on GB300 (2048^2 to 256^2 phantoms, all four TV types): column-strip
-  // kernels. Below about 448^2, where too few regions fill the GPU, 32 x 32 regions
-  // with one row per thread (two 1024-thread blocks per SM) and 8 iterations per
-  // pass; 6 iterations per 64 x 64 region up to about 1536^2. Above, with a
-  // support rectangle (whose outside tiles take the neighbour-free body) 6
-  // iterations per 64 x 64 region and 4 rows per thread (225.8 against 208.8
-  // Gpixel-iter/s for 4 per 64 x 32 at 2048^2), otherwise 6 iterations per 64 x 64
-  // region with 8 rows per thread (188.3 against 181.2).
+  // measured on GB300 (phantoms of 256^2 to 2048^2, all four TV types, 200
+  // iterations, |x| <= 1 with and without a support rectangle; Gpixel-iter/s of
+  // the best configuration): column-strip kernels throughout. Small images fill
+  // too few SMs with 64-row regions, so 32 x 32 regions with one row per thread
+  // (8 iterations per pass below about 320^2: 61.9; 4 up to about 448^2: 96.1).
+  // From there 64 x 64 regions of 8 iterations: 8 rows per thread with a support
+  // rectangle (122.2 at 512^2, 158.0 at 768^2), 4 without (132.8, 159.0); 6
+  // iterations and 8 rows per thread around 1024^2 (209.5 with the rectangle,
+  // 172.9 without); above about 1280^2, 8 iterations and 4 rows per thread with
+  // the rectangle (223.6 at 1536^2, 245.0 at 2048^2: the rectangle's outside
+  // tiles take the neighbour-free body, so long passes cost little there), and
+  // without it 8 rows per thread (181.3 at 1536^2 for 8 iterations, 188.9 at
+  // 2048^2 for 6).
   const double px = (double)m * (double)n;
-  if (px < 448.0 * 448.0) return 17;
-  if (px < 1536.0 * 1536.0) return 14;
-  return cons == CONS_RECT ? 14 : 5;
+  const bool rect = cons == CONS_RECT;
+  int cfg;
+  if (px < 320.0 * 320.0) cfg = 17;
+  else if (px < 448.0 * 448.0) cfg = 16;
+  else if (px < 896.0 * 896.0) cfg = rect ? 6 : 18;
+  else if (px < 1280.0 * 1280.0) cfg = 5;
+  else if (px < 1792.0 * 1792.0) cfg = rect ? 18 : 6;
+  else cfg = rect ? 18 : 5;
+  // A stopping test ends a pass at every check, so checks every `check_every`
+  // iterations cost ceil(check_every / T) passes per interval. Where 6 iterations
+  // per pass need no more passes than 8, the same region with T = 6 recomputes a
+  // narrower halo (2.75 against 2.90 ms per 2048^2 solve with checks every 10).
+  if (check_every > 0 && (check_every + 5) / 6 <= (check_every + 7) / 8) {
+    if (cfg == 18) cfg = 14;
+    else if (cfg == 6) cfg = 5;
+  }
+  return cfg;
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -546,7 +568,7 @@ ctv_status run_denoise(const DenoiseCall& c) {
   if (cfg >= kNumCfgs || cfg < -1) return CTV_EINVAL;
   ConsDev C;
   if (!convert_constraint(c.C, c.m, c.n, &C)) return CTV_EINVAL;
-  if (cfg < 0) cfg = default_config(c.m, c.n, K, c.tv, cons_mode(C));
+  if (cfg < 0) cfg = default_config(c.m, c.n, K, c.tv, cons_mode(C), check_every);
   if (c.workspace_bytes < denoise_workspace_bytes(c.batch, c.m, c.n)) return CTV_EINVAL;
 
   cudaStream_t s = (cudaStream_t)c.stream;

@@ -23,77 +23,9 @@
 #include "gap_device.cuh"
 #include "ctv_host.h"
 #include "ctv_kernels.h"
+#include "plan_list.cuh"
 
 namespace ctv {
-
-struct PlanImg {
-  const float2* b;
-  float2* x;
-  int ld;
-  int m, n;
-  float lam, alpha;
-  int tv;
-  ConsDev C;
-  float4* q[2];
-  float4* r[2];
-  DevStats* st;
-  int tiles_x;     // pass tiles per tile row
-  int gtiles_x;    // gap tiles per tile row
-  unsigned gnblk;  // gap blocks of this image
-};
-
-struct WorkItem {
-  int img;
-  int tile;
-};
-
-struct ListPassParams {
-  const PlanImg* imgs;
-  const WorkItem* items;
-  int in_set;
-  int out_set;
-  int first;
-  int nsteps;
-  int can_stop;   // the plan has gap checks: a block first tests its image's stop flag
-  float beta[8];
-};
-
-template <int KIND, int TV, int CONS, int T, int A, int B, int C>
-__global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B, C>::MINB)
-    fgp_pass_list_kernel(ListPassParams p) {
-  using G = CfgGeom<KIND, A, B, C>;
-  const WorkItem w = p.items[blockIdx.x];
-  // fields read from global memory one by one (a register copy of the
-  // descriptor indexed by the runtime set number would live in local memory)
-  const PlanImg& d = p.imgs[w.img];
-  if (p.can_stop && *(volatile const int*)&d.st->stop) return;
-  Img I;
-  I.b = d.b;
-  I.ld = d.ld;
-  I.q_in = d.q[p.in_set];
-  I.r_in = d.r[p.in_set];
-  I.q_out = d.q[p.out_set];
-  I.r_out = d.r[p.out_set];
-  I.m = d.m;
-  I.n = d.n;
-  I.lam = d.lam;
-  I.alpha = d.alpha;
-  I.C = d.C;
-  I.r_hist = nullptr;
-  I.hist_plane = 0;
-  const int j0 = (w.tile / d.tiles_x) * (G::RH - 2 * T), k0 = (w.tile % d.tiles_x) * (G::RW - 2 * T);
-  // The extrapolation weights go through shared memory: indexing the parameter
-  // array by the runtime step number would copy the whole parameter block into
-  // local memory. (Some tile bodies have no barrier of their own, so one orders
-  // these stores before the first use.)
-  __shared__ float beta_s[8];
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) beta_s[i] = p.beta[i];
-  }
-  __syncthreads();
-  run_tile<KIND, TV, T, A, B, C, false, CONS>(I, j0, k0, beta_s, p.nsteps, p.first != 0);
-}
 
 struct ListGapParams {
   const PlanImg* imgs;
@@ -192,38 +124,6 @@ static int gap_list_blocks(int n_items) {
   return (int)(n_items < cap ? n_items : cap);
 }
 
-template <int KIND, int TV, int CONS, int T, int A, int B, int C>
-static cudaError_t launch_list_t(const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
-  using G = CfgGeom<KIND, A, B, C>;
-  if (set_attr) {
-    return cudaFuncSetAttribute(fgp_pass_list_kernel<KIND, TV, CONS, T, A, B, C>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-  }
-  fgp_pass_list_kernel<KIND, TV, CONS, T, A, B, C><<<nblocks, G::NT, G::SMEM, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int KIND, int TV, int T, int A, int B, int C>
-static cudaError_t launch_list_cons(int cons, const ListPassParams& p, int nblocks, cudaStream_t s, bool set_attr) {
-  if constexpr (KIND == 0) {
-    return launch_list_t<KIND, TV, CONS_GEN, T, A, B, C>(p, nblocks, s, set_attr);
-  } else {
-    switch (cons) {
-      case CONS_NONE: return launch_list_t<KIND, TV, CONS_NONE, T, A, B, C>(p, nblocks, s, set_attr);
-      case CONS_AMP: return launch_list_t<KIND, TV, CONS_AMP, T, A, B, C>(p, nblocks, s, set_attr);
-      case CONS_RECT: return launch_list_t<KIND, TV, CONS_RECT, T, A, B, C>(p, nblocks, s, set_attr);
-      default: return launch_list_t<KIND, TV, CONS_GEN, T, A, B, C>(p, nblocks, s, set_attr);
-    }
-  }
-}
-
-// configurations a plan can use (a subset of the pass table, to bound build time)
-#define CTV_PLAN_CONFIGS(X)   \
-  X(2, 0, 4, 64, 32, 256)     \
-  X(7, 1, 3, 2, 8, 4)         \
-  X(11, 1, 4, 2, 8, 4)        \
-  X(14, 1, 6, 2, 16, 4)
-
 static bool plan_config_ok(int cfg) {
 #define CTV_PLAN_ID(id, kind, T, A, B, C) if (cfg == id) return true;
   CTV_PLAN_CONFIGS(CTV_PLAN_ID)
@@ -231,27 +131,15 @@ static bool plan_config_ok(int cfg) {
   return false;
 }
 
-template <int TV>
-static cudaError_t launch_list_tv(int cfg, int cons, const ListPassParams& p, int nblocks, cudaStream_t s,
-                                  bool set_attr) {
-  switch (cfg) {
-#define CTV_CFG_CASE(id, kind, T, A, B, C) \
-  case id: return launch_list_cons<kind, TV, T, A, B, C>(cons, p, nblocks, s, set_attr);
-    CTV_PLAN_CONFIGS(CTV_CFG_CASE)
-#undef CTV_CFG_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
 // One launch over the work items of the images of one TV type (items sorted by
 // type), so that every launch uses the register budget of that type alone.
 static cudaError_t launch_list(int tv, int cfg, int cons, const ListPassParams& p, int nblocks, cudaStream_t s,
                                bool set_attr) {
   switch (tv) {
-    case TV1_ISO: return launch_list_tv<TV1_ISO>(cfg, cons, p, nblocks, s, set_attr);
-    case TV1_ANISO: return launch_list_tv<TV1_ANISO>(cfg, cons, p, nblocks, s, set_attr);
-    case TV2_ISO: return launch_list_tv<TV2_ISO>(cfg, cons, p, nblocks, s, set_attr);
-    default: return launch_list_tv<TV2_ANISO>(cfg, cons, p, nblocks, s, set_attr);
+    case TV1_ISO: return launch_plan_list_tv<TV1_ISO>(cfg, cons, p, nblocks, s, set_attr);
+    case TV1_ANISO: return launch_plan_list_tv<TV1_ANISO>(cfg, cons, p, nblocks, s, set_attr);
+    case TV2_ISO: return launch_plan_list_tv<TV2_ISO>(cfg, cons, p, nblocks, s, set_attr);
+    default: return launch_plan_list_tv<TV2_ANISO>(cfg, cons, p, nblocks, s, set_attr);
   }
 }
 

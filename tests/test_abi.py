@@ -79,7 +79,7 @@ def test_tune_table_host_only(lib):
     from paper_2109_05496_gb300 import api
     rect, _ = api.Constraint(amp_max=1.0, rect=(256, 256, 1792, 1792)).to_c()
     amp, _ = api.Constraint(amp_max=1.0).to_c()
-    assert lib.ctv_default_config(2048, 2048, 200, 0, ctypes.byref(rect)) == 14
+    assert lib.ctv_default_config(2048, 2048, 200, 0, ctypes.byref(rect)) == 18
     assert lib.ctv_default_config(2048, 2048, 200, 0, ctypes.byref(amp)) == 5
 
 

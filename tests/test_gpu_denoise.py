@@ -173,7 +173,7 @@ def test_dual_export_and_warm_start(tv):
 # every = 12 is a multiple of T = 3, 4, 6 (separate kernel) but not of 8.
 @pytest.mark.parametrize("tv", ["tv1_iso", "tv2_aniso"])
 @pytest.mark.parametrize("config,every", [(-1, 10), (11, 10), (11, 12), (14, 10), (14, 12), (7, 10), (7, 12),
-                                          (16, 10), (17, 12), (5, 10)])
+                                          (16, 10), (17, 12), (5, 10), (6, 10), (18, 10), (18, 12)])
 def test_gap_stopping(tv, config, every):
     m, n = 96, 80
     _, noisy = noisy_phantom(m, n, 0.1, seed=21)

@@ -15,7 +15,7 @@ import pytest
 
 from paper_2109_05496_gb300 import build
 
-UNITS = ("plan.cu", "pass_tv1.cu", "pass_gap_tv1.cu", "backward.cu", "denoise.cu")
+UNITS = ("plan.cu", "plan_list_tv1.cu", "pass_tv1.cu", "pass_gap_tv1.cu", "backward.cu", "denoise.cu")
 KERNELS = ("fgp_pass_kernel", "fgp_pass_list_kernel", "fgp_hist_pass_kernel", "adj_stream_kernel",
            "adj2_stream_kernel", "fgp_gap_kernel", "fgp_gap_list_kernel", "fgp_finalize_kernel",
            "fgp_gap_finish_kernel")
@@ -85,3 +85,22 @@ def test_default_pass_fits_two_blocks_per_sm(reports):
         regs = re.search(r"Used (\d+) registers", lines[i + 2])
         assert regs and int(regs.group(1)) <= 64, lines[i + 2]
     assert found == 4   # the four constraint specialisations
+
+
+def test_large_image_default_fits_one_block_per_sm(reports):
+    # config 18 (T = 8, 64 x 64, 1024 threads, the large-image default with a support
+    # rectangle) must fit 64 registers per thread for its 1024-thread block, without
+    # spills in the none / amplitude / rectangle specialisations
+    rep = reports["pass_tv1.cu"]
+    lines = rep.splitlines()
+    found = 0
+    for i, ln in enumerate(lines):
+        m = re.search(r"Function properties for _ZN3ctv15fgp_pass_kernelILi1ELi1ELi8ELi2ELi16ELi4ELi(\d)E", ln)
+        if not m:
+            continue
+        found += 1
+        if int(m.group(1)) < 3:
+            assert "0 bytes spill stores" in lines[i + 1], lines[i + 1]
+        regs = re.search(r"Used (\d+) registers", lines[i + 2])
+        assert regs and int(regs.group(1)) <= 64, lines[i + 2]
+    assert found == 4
