@@ -230,7 +230,7 @@ int ctv_denoise_noalloc(const void* b, void* x, int m, int n, int ld, float lamb
  * Batched denoising of many images of uneven sizes (problem (1) per image).
  * Each image has its own shape, lambda, alpha, TV type and C; all share
  * opts->max_iters, check_every and gap_tol (warm_start must be 0; config -1
- * picks 6; plans support configurations 2, 5, 6, 7, 11, 14 and 18, others return
+ * picks 5; plans support configurations 2, 5, 6, 7, 11, 14 and 18, others return
  * CTV_EUNSUPPORTED; CTV_CONFIG_AUTOTUNE makes ctv_plan_create build a plan in
  * each supported configuration in turn, time one execution of it after a
  * warm-up on the caller's images (writing their x, synchronising), and keep the fastest -

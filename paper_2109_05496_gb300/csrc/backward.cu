@@ -923,6 +923,7 @@ int ctv_unrolled_forward(const void* b, void* x, int batch, int m, int n, const 
     for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
     p.nsteps = steps;
     p.first = first ? 1 : 0;
+    p.reverse = p.reverse ^ 1;   // alternate tile order (the previous pass's last tiles are in L2)
     p.q_in = qin;
     p.r_in = rin;
     p.q_out = qo;

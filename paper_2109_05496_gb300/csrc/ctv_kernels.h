@@ -32,6 +32,7 @@ struct PassParams {
   float beta[8];
   int nsteps;
   int first;
+  int reverse;   // blocks take the tiles in reverse order (bit-identical results)
   // a pass that ends a check interval with the duality-gap terms evaluated in it
   // (gap_eval != 0, strip configurations only): each block stores its sums in its
   // slot of the image's slot array and fgp_gap_finish_kernel evaluates them

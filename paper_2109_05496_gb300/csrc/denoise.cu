@@ -293,9 +293,10 @@ dim3 pass_grid(int cfg, int m, int n, int batch) {
 
 int default_config(int m, int n, int iters, int tv, int cons, int check_every) {
   // plans of many images (plan_list.cuh lists the configurations they support):
-  // 64 x 64 regions of 8 iterations with 8 rows per thread (151.6 Gpixel-iter/s
-  // on 512 images of sides 64 to 1024 against 143.1 for 6 iterations and 4 rows)
-  if (m <= 0 || n <= 0) return 6;
+  // 64 x 64 regions with 8 rows per thread, 6 iterations per pass (on 512 images
+  // of sides 64 to 1024, two GPUs: 150.7 and 153.3 Gpixel-iter/s, against 151.6
+  // and 151.0 for 8 iterations and 143.1 and 142.4 for 4 rows per thread)
+  if (m <= 0 || n <= 0) return 5;
   if (iters < 2) return 0;
   if (m > 0 && n > 0) {
     const int t = tuned_config(m, n, tv);
@@ -666,6 +667,9 @@ ctv_status run_denoise(const DenoiseCall& c) {
         for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)k + i] : 0.f;
         p.nsteps = steps;
         p.first = first ? 1 : 0;
+        // every other pass walks the tiles in reverse order, so that it starts on
+        // the tiles the previous pass wrote last, whose q and r are still in L2
+        p.reverse = out;
         p.q_in = q_in;
         p.r_in = r_in;
         p.q_out = set_q[out];

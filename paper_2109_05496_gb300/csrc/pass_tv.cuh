@@ -46,13 +46,15 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B
   I.C = p.C;
   I.r_hist = nullptr;
   I.hist_plane = 0;
+  const int bx = p.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  const int by = p.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
   if constexpr (!GAPEV) {
-    run_tile<KIND, TV, T, A, B, C, false, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T),
+    run_tile<KIND, TV, T, A, B, C, false, CONS>(I, by * (G::RH - 2 * T), bx * (G::RW - 2 * T),
                                                 p.beta, p.nsteps, p.first != 0);
   } else {
     GapSums gs = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, false};
-    run_tile<KIND, TV, T, A, B, C, false, CONS, true>(I, blockIdx.y * (G::RH - 2 * T),
-                                                      blockIdx.x * (G::RW - 2 * T), p.beta, p.nsteps,
+    run_tile<KIND, TV, T, A, B, C, false, CONS, true>(I, by * (G::RH - 2 * T),
+                                                      bx * (G::RW - 2 * T), p.beta, p.nsteps,
                                                       p.first != 0, &gs);
     // the block's sums as FP32 pairs into its slot (fgp_gap_finish_kernel, launched
     // after this pass, evaluates them)
