@@ -63,36 +63,20 @@ __device__ __forceinline__ float2 proj_C_adj(float2 w, float2 xb, int gj, int gk
   return xb;
 }
 
-// proj_C_adj specialised like proj_C_t (kin: the pixel's column is inside the rectangle)
-template <int CONS>
-__device__ __forceinline__ float2 proj_C_adj_t(float2 w, float2 xb, int gj, int gk, bool kin, const ConsDev& c) {
-  if (CONS == CONS_NONE) return xb;
-  if (CONS == CONS_RECT && (!kin || gj < c.j0 || gj >= c.j1)) return make_float2(0.f, 0.f);
-  if (CONS == CONS_AMP || (CONS == CONS_RECT && c.amp)) {
-    const float a2 = w.x * w.x + w.y * w.y;
-    if (a2 > c.amax * c.amax) {
-      const float inv = rsqrtf(a2);
-      const float nx = w.x * inv, ny = w.y * inv;
-      const float dot = nx * xb.x + ny * xb.y;
-      const float s = c.amax * inv;
-      return make_float2(s * (xb.x - nx * dot), s * (xb.y - ny * dot));
-    }
-    return xb;
-  }
-  if (CONS == CONS_RECT) return xb;
-  return proj_C_adj(w, xb, gj, gk, c);
-}
-
 // qbar_k = yc Y + rc rbar_{k+1} and the running dL/db sum with a fixed rounding
 // sequence (yc Y rounded, then one FMA; plain rounded adds), so that every
 // reverse-step kernel, whatever the compiler fuses around it, gives the same bits
 __device__ __forceinline__ float4 q_scale(float c, float4 y) {
-  return f4(__fmul_rn(c, y.x), __fmul_rn(c, y.y), __fmul_rn(c, y.z), __fmul_rn(c, y.w));
+  const float2 a = __fmul2_rn(make_float2(c, c), make_float2(y.x, y.y));
+  const float2 b = __fmul2_rn(make_float2(c, c), make_float2(y.z, y.w));
+  return f4(a.x, a.y, b.x, b.y);
 }
 __device__ __forceinline__ float4 q_axpy(float c, float4 y, float4 q) {
-  return f4(__fmaf_rn(c, y.x, q.x), __fmaf_rn(c, y.y, q.y), __fmaf_rn(c, y.z, q.z), __fmaf_rn(c, y.w, q.w));
+  const float2 a = __ffma2_rn(make_float2(c, c), make_float2(y.x, y.y), make_float2(q.x, q.y));
+  const float2 b = __ffma2_rn(make_float2(c, c), make_float2(y.z, y.w), make_float2(q.z, q.w));
+  return f4(a.x, a.y, b.x, b.y);
 }
-__device__ __forceinline__ float2 add_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 add_rn(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // (a, b) <- J^T (a, b) for the projection of the pair (u, v) onto the ball of radius rad
 __device__ __forceinline__ void ball2_adj(float u, float v, float rad, float& a, float& b) {
@@ -257,7 +241,9 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT) fgp_hist_pass_kern
   I.C = p.C;
   I.r_hist = hist + z * p.d_stride;
   I.hist_plane = hist_plane;
-  run_tile<KIND, TV, T, A, B, C, true, CONS>(I, blockIdx.y * (G::RH - 2 * T), blockIdx.x * (G::RW - 2 * T), p.beta,
+  const int bx = p.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  const int by = p.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+  run_tile<KIND, TV, T, A, B, C, true, CONS>(I, by * (G::RH - 2 * T), bx * (G::RW - 2 * T), p.beta,
                                              p.nsteps, p.first != 0);
 }
 
@@ -369,52 +355,143 @@ struct AdjsState {
 // whether row i-1 of this lane counts toward dL/dlambda. EDGE = false: the
 // warp's 32 columns lie in [0, n - 1) and the rows in [0, m - 1), so no bounds
 // or edge tests are needed.
+// Packed FP32x2 arithmetic on (re, im) pairs (one instruction for both halves;
+// each half rounds as the scalar operation would).
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float dot2(float2 a, float2 b) {
+  const float2 t = mul2(a, b);
+  return t.x + t.y;
+}
+
+// The reverse sweep differentiates the branch of each projection that the
+// forward pass took, so every quantity that feeds x or a projection's test is
+// computed with the forward's own expressions (same association, same fused
+// multiply-adds); only the Jacobian products that follow use packed arithmetic.
+
+// J^T of the projection of the pair u onto the ball of radius rad, applied to a (packed)
+__device__ __forceinline__ float2 ball2_adj2(float2 u, float rad, float2 a) {
+  if (rad <= 0.f) return make_float2(0.f, 0.f);
+  const float nn = u.x * u.x + u.y * u.y;
+  if (nn > rad * rad) {
+    const float inv = rsqrtf(nn);
+    const float2 nu = mul2(u, p2(inv));
+    return mul2(p2(rad * inv), fma2(nu, p2(-dot2(nu, a)), a));
+  }
+  return a;
+}
+
+// J^T of the amplitude bound's projection (as proj_C_adj: the interior branch
+// wherever |w| <= amax, including w = 0 when amax = 0)
+__device__ __forceinline__ float2 amp_adj2(float2 w, float amax, float2 xb) {
+  const float a2 = w.x * w.x + w.y * w.y;
+  if (a2 > amax * amax) {
+    const float inv = rsqrtf(a2);
+    const float2 nw = mul2(w, p2(inv));
+    return mul2(p2(amax * inv), fma2(nw, p2(-dot2(nw, xb)), xb));
+  }
+  return xb;
+}
+
+// xhat = J_PC(w)^T xbar, specialised like proj_C_t
+template <int CONS>
+__device__ __forceinline__ float2 proj_C_adj_t2(float2 w, float2 xb, int gj, int gk, bool kin, const ConsDev& c) {
+  if (CONS == CONS_NONE) return xb;
+  if (CONS == CONS_RECT && (!kin || gj < c.j0 || gj >= c.j1)) return make_float2(0.f, 0.f);
+  if (CONS == CONS_AMP || (CONS == CONS_RECT && c.amp)) return amp_adj2(w, c.amax, xb);
+  if (CONS == CONS_RECT) return xb;
+  return proj_C_adj(w, xb, gj, gk, c);
+}
+
+// gbar = J_PS(g)^T qbar with g and qbar as (d1, d2) halves
+template <int TV>
+__device__ __forceinline__ void proj_S_adj2(float2 g1, float2 g2, float2& q1, float2& q2, float alpha) {
+  if (TV == TV1_ISO) {
+    const float nn = g1.x * g1.x + g1.y * g1.y + g2.x * g2.x + g2.y * g2.y;
+    if (nn > 1.f) {
+      const float inv = rsqrtf(nn);
+      const float2 n1 = mul2(g1, p2(inv)), n2 = mul2(g2, p2(inv));
+      const float2 dt = fma2(n2, q2, mul2(n1, q1));
+      const float2 md = p2(-(dt.x + dt.y));
+      q1 = mul2(p2(inv), fma2(n1, md, q1));
+      q2 = mul2(p2(inv), fma2(n2, md, q2));
+    }
+  } else if (TV == TV1_ANISO) {
+    q1 = ball2_adj2(g1, 1.f, q1);
+    q2 = ball2_adj2(g2, 1.f, q2);
+  } else {
+    const float4 r = proj_S_adj<TV>(f4(g1.x, g1.y, g2.x, g2.y), f4(q1.x, q1.y, q2.x, q2.y), alpha);
+    q1 = lo2(r);
+    q2 = hi2(r);
+  }
+}
+
+// Phases A-D for arriving row i with inputs R = r_k, B = b, Q = qbar_k of row
+// i: what of row i-1 and rbar of row i-2 are returned (rbar computed on every
+// lane and row; only the caller knows which are valid and owned); own_m says
+// whether row i-1 of this lane counts toward dL/dlambda. EDGE = false: the
+// warp's 32 columns lie in [0, n - 1) and the rows in [0, m - 1), so no bounds
+// or edge tests are needed. The complex halves go through packed FP32x2
+// instructions.
 template <int TV, int CONS, bool EDGE>
 __device__ __forceinline__ void adjs_core(const AdjParams& p, AdjsState& S, int i, const float4 R, const float2 B,
                                           const float4 Q, bool colin, bool own_m, bool kin, bool has_right, int gk,
                                           float lam, float c8, float2& wh_out, float4& rbar_out) {
   const int m = p.m;
-  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
   const bool rin = colin && (!EDGE || (unsigned)i < (unsigned)m);
   const int im = i - 1;
   const bool inm = colin && (!EDGE || (unsigned)im < (unsigned)m);
+  const float2 nlam = p2(-lam), vc8 = p2(c8);
   // A (row i): d = L^T r, w = b - lam d, x = P_C(w); e2 = x - x(right)
-  const float2 left = shfl_up2(make_float2(R.z, R.w));
+  const float2 R1 = lo2(R), R2 = hi2(R);
+  const float2 left = shfl_up2(R2);
   float2 d = z2, w = z2, x = z2;
   if (rin) {
-    d = make_float2(R.x - S.r1p.x + R.z - left.x, R.y - S.r1p.y + R.w - left.y);
-    w = make_float2(B.x - lam * d.x, B.y - lam * d.y);
+    // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1], summed left to right as in the forward
+    d = sub2(add2(sub2(R1, S.r1p), R2), left);
+    w = fma2(nlam, d, B);
     x = proj_C_t<CONS>(w, i, gk, kin, p.C);
   }
   const float2 xr = shfl_dn2(x);
-  const float2 e2 = rin && has_right ? make_float2(x.x - xr.x, x.y - xr.y) : z2;
+  const float2 e2 = rin && has_right ? sub2(x, xr) : z2;
   // B (row i-1): g = r + L x / (8 lam), gbar = J_PS(g)^T qbar, ebar = gbar / (8 lam)
-  float4 gb = z4;
+  float2 gb1 = z2, gb2 = z2;
   if (inm) {
-    const float2 e1 = !EDGE || im < m - 1 ? make_float2(S.xm.x - x.x, S.xm.y - x.y) : z2;
-    const float4 g = f4(S.Rm.x + c8 * e1.x, S.Rm.y + c8 * e1.y, S.Rm.z + c8 * S.e2m.x, S.Rm.w + c8 * S.e2m.y);
-    gb = proj_S_adj<TV>(g, S.Qm, p.alpha);
-    if (EDGE && im == m - 1) { gb.x = 0.f; gb.y = 0.f; }
-    if (!has_right) { gb.z = 0.f; gb.w = 0.f; }
-    if (own_m) S.lacc -= 8.f * c8 * c8 * (gb.x * e1.x + gb.y * e1.y + gb.z * S.e2m.x + gb.w * S.e2m.y);
+    const float2 e1 = !EDGE || im < m - 1 ? sub2(S.xm, x) : z2;
+    const float2 g1 = fma2(vc8, e1, lo2(S.Rm)), g2 = fma2(vc8, S.e2m, hi2(S.Rm));
+    gb1 = lo2(S.Qm);
+    gb2 = hi2(S.Qm);
+    proj_S_adj2<TV>(g1, g2, gb1, gb2, p.alpha);
+    if (EDGE && im == m - 1) gb1 = z2;
+    if (!has_right) gb2 = z2;
+    if (own_m) {
+      const float2 t = fma2(gb2, S.e2m, mul2(gb1, e1));
+      S.lacc -= 8.f * c8 * c8 * (t.x + t.y);
+    }
   }
-  const float2 eb1 = make_float2(c8 * gb.x, c8 * gb.y), eb2 = make_float2(c8 * gb.z, c8 * gb.w);
+  const float2 eb1 = mul2(vc8, gb1), eb2 = mul2(vc8, gb2);
   // C (row i-1): xbar = L^T ebar, what = J_PC(w)^T xbar
   const float2 ebl = shfl_up2(eb2);
   float2 wh = z2;
   if (inm) {
-    const float2 xb = make_float2(eb1.x - S.eb1m.x + eb2.x - ebl.x, eb1.y - S.eb1m.y + eb2.y - ebl.y);
-    wh = proj_C_adj_t<CONS>(S.wm, xb, im, gk, kin, p.C);
-    if (own_m) S.lacc -= S.dm.x * wh.x + S.dm.y * wh.y;
+    const float2 xb = add2(sub2(eb1, S.eb1m), sub2(eb2, ebl));
+    wh = proj_C_adj_t2<CONS>(S.wm, xb, im, gk, kin, p.C);
+    if (own_m) S.lacc -= dot2(S.dm, wh);
   }
   const float2 whr = shfl_dn2(wh);
-  const float2 d2 = inm && has_right ? make_float2(wh.x - whr.x, wh.y - whr.y) : z2;
+  const float2 d2 = inm && has_right ? sub2(wh, whr) : z2;
   // D (row i-2): rbar = gbar - lam L what
-  const float2 d1 = !EDGE || i - 2 < m - 1 ? make_float2(S.whmm.x - wh.x, S.whmm.y - wh.y) : z2;
-  rbar_out = f4(S.gbmm.x - lam * d1.x, S.gbmm.y - lam * d1.y, S.gbmm.z - lam * S.d2mm.x, S.gbmm.w - lam * S.d2mm.y);
+  const float2 d1 = !EDGE || i - 2 < m - 1 ? sub2(S.whmm, wh) : z2;
+  const float2 rb1 = fma2(nlam, d1, lo2(S.gbmm)), rb2 = fma2(nlam, S.d2mm, hi2(S.gbmm));
+  rbar_out = f4(rb1.x, rb1.y, rb2.x, rb2.y);
   wh_out = wh;
-  S.r1p = make_float2(R.x, R.y);
+  S.r1p = R1;
   S.Rm = R;
   S.Qm = Q;
   S.wm = w;
@@ -422,7 +499,7 @@ __device__ __forceinline__ void adjs_core(const AdjParams& p, AdjsState& S, int 
   S.xm = x;
   S.e2m = e2;
   S.eb1m = eb1;
-  S.gbmm = gb;
+  S.gbmm = f4(gb1.x, gb1.y, gb2.x, gb2.y);
   S.whmm = wh;
   S.d2mm = d2;
 }
@@ -1024,6 +1101,7 @@ int ctv_unrolled_backward(const void* b, const void* xbar, void* bbar, float* la
       for (int i = 0; i < 8; ++i) p.beta[i] = i < steps ? (float)beta[(size_t)kk + i] : 0.f;
       p.nsteps = steps;
       p.first = first ? 1 : 0;
+      p.reverse = p.reverse ^ 1;   // alternate tile order, as in the forward
       p.q_in = qin;
       p.r_in = rin;
       // the last recompute pass of a segment keeps only its r_k history
