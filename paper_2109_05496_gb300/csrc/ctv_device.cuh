@@ -446,8 +446,9 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
   // the loop-carried registers need no copies between steps. With eight rows
   // the unrolled steps need more than the 128 registers a thread may have
   // (spills), and with one row (1024-thread blocks of small images) it was
-  // measured slower, so those keep the loop.
-  constexpr int STEP_UNROLL = (PPT == 2 || PPT == 4) ? T : 1;
+  // measured slower, so those keep the loop; so do recompute tiles (HIST),
+  // whose per-step history stores made the unrolled loop spill at 64 registers.
+  constexpr int STEP_UNROLL = (!HIST && (PPT == 2 || PPT == 4)) ? T : 1;
 #pragma unroll STEP_UNROLL
   for (int it = 0; it < T; ++it) {
     if (it >= nsteps) break;
