@@ -355,20 +355,6 @@ struct AdjsState {
 // whether row i-1 of this lane counts toward dL/dlambda. EDGE = false: the
 // warp's 32 columns lie in [0, n - 1) and the rows in [0, m - 1), so no bounds
 // or edge tests are needed.
-// Packed FP32x2 arithmetic on (re, im) pairs (one instruction for both halves;
-// each half rounds as the scalar operation would).
-__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ float dot2(float2 a, float2 b) {
-  const float2 t = mul2(a, b);
-  return t.x + t.y;
-}
-
 // The reverse sweep differentiates the branch of each projection that the
 // forward pass took, so every quantity that feeds x or a projection's test is
 // computed with the forward's own expressions (same association, same fused

@@ -43,6 +43,20 @@ struct DevStats {
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 
+// Packed FP32x2 arithmetic on (re, im) pairs (one instruction for both halves;
+// each half rounds as the scalar operation would).
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float dot2(float2 a, float2 b) {
+  const float2 t = mul2(a, b);
+  return t.x + t.y;
+}
+
 // Non-finite test of one complex input value (NaN or an infinity in either part).
 __device__ __forceinline__ bool nonfinite2(float2 v) { return !(isfinite(v.x) && isfinite(v.y)); }
 
@@ -148,6 +162,9 @@ __device__ __forceinline__ float2 proj_C(float2 w, int gj, int gk, const ConsDev
 // P_S for the four TV types. g = (r1, s1, r2, s2).
 #ifndef CTV_BRANCHLESS_PS
 #define CTV_BRANCHLESS_PS 1
+#endif
+#ifndef CTV_PACK8
+#define CTV_PACK8 1         // packed FP32x2 arithmetic in the 8-rows-per-thread strip body
 #endif
 
 
@@ -427,6 +444,14 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
   // support rectangle, so their edge path needs no per-pixel image test in
   // the iterations; the general constraint (mask, box) keeps the tests.
   constexpr bool TESTS = EDGE && CONS == CONS_GEN;
+  // Eight rows per thread (a 128-register budget) take the complex halves
+  // through packed FP32x2 instructions, associated as the scalar form so the
+  // results are the same bits. Measured against the scalar form: T = 6 (config
+  // 5) +1.0% at 2048^2, +2.4% at 1024^2, +5.4% on a plan of 512 images; T = 8
+  // (config 6) -1.7% at 2048^2; recompute tiles spilled. Under the 64-register
+  // budgets of the other configurations the register pairs cost more than they
+  // save (config 11 and 14: 167 / 164 -> 144 / 139 Gpixel-iter/s).
+  constexpr bool PACK = CTV_PACK8 && PPT == 8 && T <= 6 && !HIST;
   // Rows whose values can still reach the interior after the remaining steps:
   // step it must produce q, r on rows [lo, RH - lo) and x on one more row, with
   // lo = T - (nsteps - 1 - it). With few rows per thread the rows outside are
@@ -466,11 +491,16 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
         if (s > 0) up = make_float2(r[s - 1].x, r[s - 1].y);
         else up = wy > 0 ? P1B[(wy - 1) * RW + lk] : z2;
         const float2 left = lk > 0 ? P2[(lj0 + s) * RW + lk - 1] : z2;
-        // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]
-        const float dre = r[s].x - up.x + r[s].z - left.x;
-        const float dim = r[s].y - up.y + r[s].w - left.y;
         const float2 bb = Bs[(lj0 + s) * RW + lk];
-        x[s] = proj_C_t<CONS>(make_float2(bb.x - lam * dre, bb.y - lam * dim), gj, gk, kin, I.C);
+        // (L^T p)[j,k] = p1[j,k] - p1[j-1,k] + p2[j,k] - p2[j,k-1]
+        if constexpr (PACK) {
+          const float2 d = sub2(add2(sub2(lo2(r[s]), up), hi2(r[s])), left);
+          x[s] = proj_C_t<CONS>(fma2(p2(-lam), d, bb), gj, gk, kin, I.C);
+        } else {
+          const float dre = r[s].x - up.x + r[s].z - left.x;
+          const float dim = r[s].y - up.y + r[s].w - left.y;
+          x[s] = proj_C_t<CONS>(make_float2(bb.x - lam * dre, bb.y - lam * dim), gj, gk, kin, I.C);
+        }
       }
       X[(lj0 + s) * RW + lk] = x[s];
     }
@@ -482,24 +512,32 @@ __device__ __forceinline__ void fgp_strip_body(const Img& I, int j0, int k0, con
       const int gj = gj0 + s;
       if (SKIP_ROWS && CTV_ROW_SKIP(lj0 + s < lo || lj0 + s >= hi)) continue;
       if (!TESTS || (colin && (unsigned)gj < (unsigned)I.m)) {
-        float d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+        float2 e1 = z2, e2 = z2;   // (L x)[j,k]: x[j,k] - x[j+1,k] and x[j,k] - x[j,k+1]
         if (!EDGE || (gj >= 0 && gj < I.m - 1)) {
           float2 xd;
           if (s < PPT - 1) xd = x[s + 1];
           else xd = strip_bottom_in ? X[(lj0 + s + 1) * RW + lk] : x[s];
-          d1r = x[s].x - xd.x;
-          d1i = x[s].y - xd.y;
+          e1 = PACK ? sub2(x[s], xd) : make_float2(x[s].x - xd.x, x[s].y - xd.y);
         }
         if (has_right) {
           const float2 xr = X[(lj0 + s) * RW + lk + 1];
-          d2r = x[s].x - xr.x;
-          d2i = x[s].y - xr.y;
+          e2 = PACK ? sub2(x[s], xr) : make_float2(x[s].x - xr.x, x[s].y - xr.y);
         }
-        const float4 qn = proj_S<TV>(f4(r[s].x + c8 * d1r, r[s].y + c8 * d1i, r[s].z + c8 * d2r, r[s].w + c8 * d2i),
-                                     I.alpha);
-        r[s] = f4(qn.x + bt * (qn.x - q[s].x), qn.y + bt * (qn.y - q[s].y),
-                  qn.z + bt * (qn.z - q[s].z), qn.w + bt * (qn.w - q[s].w));
-        q[s] = qn;
+        if constexpr (PACK) {
+          const float2 g1 = fma2(p2(c8), e1, lo2(r[s]));
+          const float2 g2 = fma2(p2(c8), e2, hi2(r[s]));
+          const float4 qn = proj_S<TV>(f4(g1.x, g1.y, g2.x, g2.y), I.alpha);
+          const float2 n1 = fma2(p2(bt), sub2(lo2(qn), lo2(q[s])), lo2(qn));
+          const float2 n2 = fma2(p2(bt), sub2(hi2(qn), hi2(q[s])), hi2(qn));
+          r[s] = f4(n1.x, n1.y, n2.x, n2.y);
+          q[s] = qn;
+        } else {
+          const float4 qn = proj_S<TV>(
+              f4(r[s].x + c8 * e1.x, r[s].y + c8 * e1.y, r[s].z + c8 * e2.x, r[s].w + c8 * e2.y), I.alpha);
+          r[s] = f4(qn.x + bt * (qn.x - q[s].x), qn.y + bt * (qn.y - q[s].y),
+                    qn.z + bt * (qn.z - q[s].z), qn.w + bt * (qn.w - q[s].w));
+          q[s] = qn;
+        }
         if (HIST && lk >= T && lk < RW - T && lj0 + s >= T && lj0 + s < RH - T &&
             (!EDGE || (colin && (unsigned)gj < (unsigned)I.m)))
           I.r_hist[it * I.hist_plane + (long long)gj * I.n + gk] = r[s];
