@@ -59,15 +59,8 @@ __global__ void __launch_bounds__(CfgGeom<KIND, A, B, C>::NT, CfgGeom<KIND, A, B
     // the block's sums as FP32 pairs into its slot (fgp_gap_finish_kernel, launched
     // after this pass, evaluates them)
     __shared__ float2 red[3 * (G::NT / 32)];
-    float hs[3], ls[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      hs[a] = gs.s[a];
-      ls[a] = -gs.c[a];
-    }
-    block_sum_pairs<G::NT, 3>(hs, ls, red);
-    const bool block_nf = __syncthreads_or(gs.nf) != 0;
-    gap_store_slot(p.gst + z, p.slots + z * p.slot_stride, blockIdx.y * gridDim.x + blockIdx.x, hs, ls, block_nf);
+    gap_block_store<G::NT>(gs, I.lam, p.gst + z, p.slots + z * p.slot_stride, blockIdx.y * gridDim.x + blockIdx.x,
+                           red);
   }
 }
 
