@@ -95,3 +95,20 @@ def test_config_table_matches_library(lib):
             assert (w.value, h.value, nt.value) == (A, B, C)
         else:
             assert (w.value, h.value, nt.value) == (32 * A, B * C, 32 * A * B)
+
+
+def test_default_configuration_by_size(lib):
+    # the measured size rule of the untuned default (no tuned entry for these
+    # classes in a fresh process): 32 x 32 regions for small images, 64 x 64
+    # regions above, the depth and rows per thread depending on size and on
+    # whether a support rectangle makes the outside tiles cheap
+    import ctypes
+    from paper_2109_05496_gb300 import api
+    rect, _ = api.Constraint(amp_max=1.0, rect=(1, 1, 2, 2)).to_c()
+    amp, _ = api.Constraint(amp_max=1.0).to_c()
+    want = {256: (17, 17), 384: (16, 16), 512: (6, 18), 768: (6, 18), 1024: (5, 5), 1536: (18, 6), 2048: (18, 5),
+            4096: (18, 5)}
+    for side, (w_rect, w_amp) in want.items():
+        assert lib.ctv_default_config(side, side, 200, 0, ctypes.byref(rect)) == w_rect, side
+        assert lib.ctv_default_config(side, side, 200, 0, ctypes.byref(amp)) == w_amp, side
+    assert lib.ctv_default_config(2048, 2048, 200, 0, None) == 5   # no constraint: as the amplitude bound
