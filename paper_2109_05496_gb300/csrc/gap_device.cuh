@@ -187,9 +187,9 @@ __device__ __forceinline__ void gap_store_slot(DevStats* st, float* slots, unsig
 // FP32 (a warp's partial covers up to 128 pixels, its relative rounding error is
 // below 5 units in the last place, 3e-7, and unbiased, so about 2e-9 of the
 // image's total over its tens of thousands of warps), across warps in FP32
-// pairs. Measured on a 2048^2 pass with checks every 10 iterations: 53.8 us per
-// check with three pair sums reduced in pairs at every level, 49.0 with two of
-// them and plain FP32 over the first three levels.
+// pairs. Measured side by side on 2048^2 solves with checks every 10
+// iterations: 54.8 us per check with three sums reduced in pairs at every level,
+// 49.4 us in this form.
 template <int NT>
 __device__ __forceinline__ void gap_block_store(const GapSums& gs, float lam, DevStats* st, float* slots,
                                                 unsigned blk, float2* red) {
