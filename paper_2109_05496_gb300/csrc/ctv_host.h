@@ -29,6 +29,15 @@ struct DenoiseCall {
   ctv_stats* stats;
   ctv_stream stream;
   int plain_launches;   // nonzero: never build a stop graph (callers that must not allocate)
+  // Algorithm 1's momentum folded into the finalize (one image; phase retrieval):
+  // when the solve ends with the x-only finalize, it also writes
+  // z = x + mom_beta (x - mom_xprev) (x_prev with x's row stride) to mom_z (row
+  // stride mom_ld) and sets *mom_written; otherwise the caller forms z itself.
+  float2* mom_z;
+  int mom_ld;
+  const float2* mom_xprev;
+  float mom_beta;
+  int* mom_written;
 };
 
 // Facts that hold for one device - a kernel's shared-memory limit, the SM count,

@@ -61,6 +61,11 @@ struct GapParams {
   const float* lam_dev;
   float alpha;
   ConsDev C;
+  // x-only finalize of one image: optionally z = x + mom_beta (x - mom_xprev) too
+  float2* mom_z;
+  int mom_ld;
+  const float2* mom_xprev;
+  float mom_beta;
   DevStats* st;
   float* slots;           // block partial sums of the reduction (slot_stride floats per image)
   long long slot_stride;

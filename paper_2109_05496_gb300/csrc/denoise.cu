@@ -198,10 +198,16 @@ __global__ void __launch_bounds__(FIN_NT) fgp_finalize_kernel(GapParams p) {
     }
     const float2 bb = __ldg(b + (long long)j * p.ld + k);
     nf |= nonfinite2(bb);
-    x[(long long)j * p.ld + k] =
+    const float2 xv =
         proj_C(make_float2(fmaf(-lam, qc.x - qu.x + qc.z - ql.z, bb.x), fmaf(-lam, qc.y - qu.y + qc.w - ql.w, bb.y)), j, k,
                p.C);
+    x[(long long)j * p.ld + k] = xv;
     if (qe != nullptr) qe[o] = qc;
+    if (p.mom_z != nullptr) {   // Alg. 1, step 5, as pr_fista forms it
+      const float2 xp = __ldg(p.mom_xprev + (long long)j * p.ld + k);
+      p.mom_z[(long long)j * p.mom_ld + k] =
+          make_float2(fmaf(p.mom_beta, xv.x - xp.x, xv.x), fmaf(p.mom_beta, xv.y - xp.y, xv.y));
+    }
   }
   // a NaN or infinity in b: one report per warp (the threads past column n have returned)
   const unsigned am = __activemask();
@@ -773,6 +779,13 @@ ctv_status run_denoise(const DenoiseCall& c) {
     if (warm && last_set < 0 && gg.q_export == gg.dual_in) gg.q_export = nullptr;  // unchanged
     // without gap checks and with nobody reading the statistics, only x (and q) are written
     const bool light = c.stats == nullptr && check_every == 0;
+    if (light && c.mom_z != nullptr && c.batch == 1) {
+      gg.mom_z = c.mom_z;
+      gg.mom_ld = c.mom_ld;
+      gg.mom_xprev = c.mom_xprev;
+      gg.mom_beta = c.mom_beta;
+      if (c.mom_written != nullptr) *c.mom_written = 1;
+    }
     if ((light ? launch_finalize(gg, c.batch, es) : launch_gap(c.tv, gg, c.batch, es)) != cudaSuccess)
       return CTV_ECUDA;
     count_launches(light ? 1 : 2);

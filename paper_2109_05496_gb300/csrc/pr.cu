@@ -11,7 +11,9 @@
 //                 reduced in FP64 (Eq. (24), (27); xi/|xi| := 1 at xi = 0)
 //   pr_form_v     v = z - gamma grad F(z)           (Alg. 1, step 3, gradient at z_k)
 //   pr_fista      z_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1})   (Alg. 1, steps 4-5),
-//                 written straight into the padded buffer
+//                 written straight into the padded buffer; when the inner solve ends
+//                 with the x-only finalize (no gap checks), that kernel forms z_{k+1}
+//                 in the same pass over x instead (same arithmetic, one launch less)
 // The prox of gamma (tau TV + I_C) is problem (15) with lam = tau gamma, solved by
 // the fused FGP path, warm-started from the previous outer iteration's dual.
 #include <cuda_runtime.h>
@@ -110,7 +112,7 @@ __global__ void pr_fista(const float2* __restrict__ X, const float2* __restrict_
   if (k >= n) return;
   const float2 x = X[(long long)j * ldX + k];
   const float2 xp = Xp[(long long)j * ldX + k];
-  Z[(long long)j * ldZ + k] = make_float2(x.x + beta * (x.x - xp.x), x.y + beta * (x.y - xp.y));
+  Z[(long long)j * ldZ + k] = make_float2(fmaf(beta, x.x - xp.x, x.x), fmaf(beta, x.y - xp.y, x.y));
 }
 
 // Sufficient-decrease terms of the backtracking line search:
@@ -340,21 +342,26 @@ int ctv_pr_solve(ctv_pr_plan* p, const float* sqrt_y, const void* H, float tau, 
     pr_form_v<<<g, 256, 0, s>>>(p->P, p->N, p->F, p->N, gamma * inv, p->V, n, m, n);
     count_launch();
     o.warm_start = k > 0 ? 1 : 0;
-    DenoiseCall c;
-    memset(&c, 0, sizeof(c));
-    c.b = p->V; c.x = p->X[cur]; c.batch = 1; c.m = m; c.n = n; c.ld = n;
-    c.lam = lam; c.C = C; c.tv = tv_type; c.opts = &o; c.dual_state = p->dual;
-    c.workspace = p->fgp_ws; c.workspace_bytes = p->fgp_ws_bytes; c.stats = nullptr; c.stream = stream;
-    st = run_denoise(c);
-    if (st != CTV_OK) return st;
     float beta = 0.f;
     if (accelerate) {
       const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
       beta = (float)((t - 1.0) / tn);
       t = tn;
     }
-    pr_fista<<<g, 256, 0, s>>>(p->X[cur], p->X[cur ^ 1], n, beta, p->P, p->N, m, n);
-    count_launch();
+    // the inner solve's finalize also forms z_{k+1} when it is the x-only one
+    int fused = 0;
+    DenoiseCall c;
+    memset(&c, 0, sizeof(c));
+    c.b = p->V; c.x = p->X[cur]; c.batch = 1; c.m = m; c.n = n; c.ld = n;
+    c.lam = lam; c.C = C; c.tv = tv_type; c.opts = &o; c.dual_state = p->dual;
+    c.workspace = p->fgp_ws; c.workspace_bytes = p->fgp_ws_bytes; c.stats = nullptr; c.stream = stream;
+    c.mom_z = p->P; c.mom_ld = p->N; c.mom_xprev = p->X[cur ^ 1]; c.mom_beta = beta; c.mom_written = &fused;
+    st = run_denoise(c);
+    if (st != CTV_OK) return st;
+    if (!fused) {
+      pr_fista<<<g, 256, 0, s>>>(p->X[cur], p->X[cur ^ 1], n, beta, p->P, p->N, m, n);
+      count_launch();
+    }
     cur ^= 1;
   }
   // the last x_k sits in X[cur ^ 1]
@@ -472,10 +479,15 @@ int ctv_prox_grad_step(const void* z, const void* grad, float gamma, float tau, 
   c.b = V; c.x = x_out; c.batch = 1; c.m = m; c.n = n; c.ld = n;
   c.lam = tau * gamma; c.C = C; c.tv = tv_type; c.opts = inner; c.dual_state = dual_state;
   c.workspace = fws; c.workspace_bytes = denoise_workspace_bytes(1, m, n); c.stats = nullptr; c.stream = stream;
+  int fused = 0;
+  c.mom_z = (float2*)z_next; c.mom_ld = n; c.mom_xprev = (const float2*)x_prev; c.mom_beta = beta;
+  c.mom_written = &fused;
   ctv_status st = run_denoise(c);
   if (st != CTV_OK) return st;
-  pr_fista<<<g, 256, 0, s>>>((const float2*)x_out, (const float2*)x_prev, n, beta, (float2*)z_next, n, m, n);
-  count_launch();
+  if (!fused) {
+    pr_fista<<<g, 256, 0, s>>>((const float2*)x_out, (const float2*)x_prev, n, beta, (float2*)z_next, n, m, n);
+    count_launch();
+  }
   return cudaGetLastError() == cudaSuccess ? CTV_OK : CTV_ECUDA;
 }
 

@@ -116,6 +116,41 @@ def test_prox_grad_step_matches_oracle():
     assert np.abs(zn_g.cpu().numpy() - zo).max() <= 2e-4 * np.abs(v).max()
 
 
+def test_momentum_folded_into_finalize():
+    # Alg. 1, step 5: an inner solve without gap checks ends with the x-only
+    # finalize, which also forms z_{k+1} = x + beta (x - x_prev); with gap checks it
+    # ends with the gap kernel and the separate momentum kernel forms z. On both
+    # paths z is that expression of the returned x to the last unit (one fused
+    # multiply-add per part; numpy evaluates it in FP64 and rounds once more).
+    m, n = 61, 90
+    rng = np.random.default_rng(12)
+    z = (0.8 * np.exp(1j * rng.uniform(0, 3, (m, n)))).astype(np.complex64)
+    grad = (0.1 * (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))).astype(np.complex64)
+    xp = (0.7 * np.exp(1j * rng.uniform(0, 3, (m, n)))).astype(np.complex64)
+    zg, gg, xpg = to_gpu(z, grad, xp)
+    beta = np.float32(0.37)
+    xs = []
+    for opts in (ctv.make_opts(12, alpha=0.5), ctv.make_opts(12, 5, 0.0, 0.5)):
+        xo_g = torch.empty_like(zg)
+        zn_g = torch.empty_like(zg)
+        ctv.ctv_prox_grad_step(zg, gg, 0.9, 0.03, ctv.Constraint(amp_max=1.0), "tv1_iso", opts, None, xpg,
+                               xo_g, zn_g, float(beta))
+        torch.cuda.synchronize()
+        x = xo_g.cpu().numpy()
+        zn = zn_g.cpu().numpy()
+        for part in (np.real, np.imag):
+            xa, pa = part(x).astype(np.float32), part(xp).astype(np.float32)
+            d = (xa - pa).astype(np.float32)
+            want = (xa.astype(np.float64) + np.float64(beta) * d.astype(np.float64)).astype(np.float32)
+            got = part(zn).astype(np.float32)
+            ulp = np.spacing(np.maximum(np.abs(want), np.abs(got)))
+            assert np.all(np.abs(got - want) <= ulp)
+        xs.append(x)
+    # the two schedules differ only by FP32 rounding (the check-evaluating pass is
+    # compiled separately)
+    assert np.abs(xs[0] - xs[1]).max() <= 1e-6
+
+
 def test_full_size_first_iterations_and_convergence():
     # the phase-retrieval workload: 1024^2 object, Fresnel TF (532 nm, 2 um, 5 mm), 2x padding,
     # Poisson noise at 1e4 photons; first two outer iterations element by element, then a
