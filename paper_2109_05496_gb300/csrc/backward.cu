@@ -92,21 +92,13 @@ __device__ __forceinline__ void ball2_adj(float u, float v, float rad, float& a,
   }
 }
 
-// gbar = J_PS(g)^T qbar for the four TV types; g = (r1, s1, r2, s2)
+// gbar = J_PS(g)^T qbar for the type-II TV types, whose balls pair the real
+// parts of the two differences and the imaginary parts (Eq. (35)) or clamp each
+// component (Eq. (37)); g = (r1, s1, r2, s2). (Type I: proj_S_adj2.)
 template <int TV>
-__device__ __forceinline__ float4 proj_S_adj(float4 g, float4 qb, float alpha) {
-  if (TV == TV1_ISO) {
-    const float nn = g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w;
-    if (nn > 1.f) {
-      const float inv = rsqrtf(nn);
-      const float4 n = f4(g.x * inv, g.y * inv, g.z * inv, g.w * inv);
-      const float dot = n.x * qb.x + n.y * qb.y + n.z * qb.z + n.w * qb.w;
-      qb = f4(inv * (qb.x - n.x * dot), inv * (qb.y - n.y * dot), inv * (qb.z - n.z * dot), inv * (qb.w - n.w * dot));
-    }
-  } else if (TV == TV1_ANISO) {
-    ball2_adj(g.x, g.y, 1.f, qb.x, qb.y);
-    ball2_adj(g.z, g.w, 1.f, qb.z, qb.w);
-  } else if (TV == TV2_ISO) {
+__device__ __forceinline__ float4 proj_S_adj_type2(float4 g, float4 qb, float alpha) {
+  static_assert(TV == TV2_ISO || TV == TV2_ANISO, "type-II TV only");
+  if (TV == TV2_ISO) {
     ball2_adj(g.x, g.z, alpha, qb.x, qb.z);
     ball2_adj(g.y, g.w, 1.f - alpha, qb.y, qb.w);
   } else {
@@ -397,7 +389,7 @@ __device__ __forceinline__ float2 proj_C_adj_t2(float2 w, float2 xb, int gj, int
 // gbar = J_PS(g)^T qbar with g and qbar as (d1, d2) halves
 template <int TV>
 __device__ __forceinline__ void proj_S_adj2(float2 g1, float2 g2, float2& q1, float2& q2, float alpha) {
-  if (TV == TV1_ISO) {
+  if constexpr (TV == TV1_ISO) {
     const float nn = g1.x * g1.x + g1.y * g1.y + g2.x * g2.x + g2.y * g2.y;
     if (nn > 1.f) {
       const float inv = rsqrtf(nn);
@@ -407,11 +399,11 @@ __device__ __forceinline__ void proj_S_adj2(float2 g1, float2 g2, float2& q1, fl
       q1 = mul2(p2(inv), fma2(n1, md, q1));
       q2 = mul2(p2(inv), fma2(n2, md, q2));
     }
-  } else if (TV == TV1_ANISO) {
+  } else if constexpr (TV == TV1_ANISO) {
     q1 = ball2_adj2(g1, 1.f, q1);
     q2 = ball2_adj2(g2, 1.f, q2);
   } else {
-    const float4 r = proj_S_adj<TV>(f4(g1.x, g1.y, g2.x, g2.y), f4(q1.x, q1.y, q2.x, q2.y), alpha);
+    const float4 r = proj_S_adj_type2<TV>(f4(g1.x, g1.y, g2.x, g2.y), f4(q1.x, q1.y, q2.x, q2.y), alpha);
     q1 = lo2(r);
     q2 = hi2(r);
   }
